@@ -1,0 +1,190 @@
+/*
+ * tc.h — C ABI of the GB300 triangle-counting / k-truss library.
+ *
+ * The library implements the kernels of the Static Graph Challenge
+ * (Samsi et al., "Static Graph Challenge: Subgraph Isomorphism", 2017):
+ * triangle counting (Section III-A), per-edge triangle support and k-truss
+ * peeling with the truss decomposition (Section III-B, Algorithm 4).  All
+ * computation runs in hand-written CUDA kernels on one GPU; there is no CPU
+ * fallback.
+ *
+ * Conventions shared by every call
+ *  - Vertex ids are 0-based int32 in [0, n).  (The Challenge's TSV files are
+ *    1-based, Section II; a caller converts them.)
+ *  - Edge ids: after cleaning, the graph's undirected edges are listed as
+ *    pairs (lo, hi), lo < hi, in lexicographic order of the ORIGINAL ids
+ *    (the "canonical edge list").  An edge's position in that list is its
+ *    edge id, and every per-edge output is indexed by it.
+ *  - Pointers: the caller owns every input and output buffer.  Array
+ *    arguments may be device memory or host memory (pageable or pinned);
+ *    the library inspects each pointer and copies through the device when
+ *    it is on the host.  Scalar outputs (triangles_out, edges_out,
+ *    kmax_out) are host pointers.
+ *  - Streams: `cuda_stream` is a cudaStream_t (NULL = the legacy default
+ *    stream).  Work is ordered on that stream.  A call that returns a host
+ *    scalar, or writes a host array, synchronises that stream before
+ *    returning; a call whose outputs are all device arrays returns without
+ *    synchronising.
+ *  - Memory: a tc_graph and the scratch of every call are allocated by the
+ *    library from the device's stream-ordered pool (cudaMallocAsync) on the
+ *    call's stream, on the device current at tc_build_csr.
+ *  - Errors: every int-returning call returns TC_OK (0) or a negative
+ *    TC_E* code; no exception crosses the ABI.  tc_strerror names a code and
+ *    tc_last_error describes the calling thread's most recent failure.
+ *  - Threads: distinct graphs may be used concurrently from distinct threads
+ *    on distinct streams; one graph must not be used by two calls at once.
+ */
+#ifndef TC_GB300_H
+#define TC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tc_graph tc_graph; /* opaque, device-resident, owned by the library */
+
+enum {
+    TC_OK = 0,
+    TC_EINVAL = -1,     /* null pointer, n <= 0, m_in < 0, k < 2, bad flags */
+    TC_ERANGE = -2,     /* a vertex id outside [0, n) */
+    TC_ENOMEM = -3,     /* a device or host allocation failed */
+    TC_ECUDA = -4,      /* a CUDA runtime call or kernel launch failed */
+    TC_ETIMEDOUT = -5,  /* a bounded device-side wait gave up */
+    TC_EOVERFLOW = -6   /* more than 2^31 - 1 edges after cleaning */
+};
+
+/* Flags of tc_build_csr: where src/dst live (AUTO inspects the pointers). */
+enum { TC_INPUT_AUTO = 0, TC_INPUT_DEVICE = 1, TC_INPUT_HOST = 2 };
+
+/*
+ * tc_build_csr — clean an edge list and build the device graph.
+ *
+ * Follows Section II's input rules: vertex ids in [0, n), self-loops dropped,
+ * a directed pair (u, v) stands for the undirected edge {u, v}, repeated
+ * pairs collapse to one edge, weights are 1.  Builds on the device:
+ *   - the canonical edge list (see above);
+ *   - vertex degrees and a degree order rank(v) = position of (deg(v), v);
+ *   - a symmetric CSR over rank ids whose rows are sorted, with the edge id
+ *     of every entry; the part of row u above u is the out-list N+(u) of the
+ *     degree-oriented adjacency L used by tc_count / tc_edge_support.
+ * src, dst: m_in int32 endpoints each (device or host, see flags).
+ * m_in >= 0 (0 gives an empty graph); n >= 1.
+ * flags: TC_INPUT_AUTO / TC_INPUT_DEVICE / TC_INPUT_HOST.
+ * out: receives the new graph (freed with tc_graph_free); untouched on error.
+ * Inputs are not retained after the call returns.
+ * Errors: TC_EINVAL (null pointers with m_in > 0, n < 1, m_in < 0),
+ * TC_ERANGE (an id outside [0, n); no graph is returned), TC_EOVERFLOW,
+ * TC_ENOMEM, TC_ECUDA, TC_ETIMEDOUT.
+ */
+int tc_build_csr(const int32_t* src, const int32_t* dst, int64_t m_in, int32_t n, int flags,
+                 void* cuda_stream, tc_graph** out);
+
+/*
+ * tc_count — number of triangles (Section III-A).
+ *
+ * Computes the masked product (L L^T) ∘ L over the degree-oriented adjacency
+ * L (the once-per-triangle form of Algorithm 3): for every oriented edge
+ * (u, v), |N+(u) ∩ N+(v)|, summed.  Exact int64.
+ * triangles_out: host int64.  Synchronises the stream.
+ */
+int tc_count(tc_graph* g, int64_t* triangles_out, void* cuda_stream);
+
+/*
+ * tc_edge_support — triangle support of every edge (Algorithm 4,
+ * s = (R == 2) 1 with R = E A): s[e] = number of triangles containing e.
+ * Every triangle found by the masked product credits its three edges.
+ * support_out: m int32 in edge-id order (device or host).
+ * triangles_out: host int64, may be NULL (then, with a device support_out,
+ * the call does not synchronise).
+ */
+int tc_edge_support(tc_graph* g, int32_t* support_out, int64_t* triangles_out,
+                    void* cuda_stream);
+
+/*
+ * ktruss — the k-truss (Section III-B): the largest subgraph in which every
+ * edge lies in at least k - 2 triangles of the subgraph.  Edges whose
+ * support is below k - 2 are removed in bulk rounds and the supports of the
+ * edges sharing their triangles are lowered, until no edge is below
+ * (Algorithm 4's loop).  k >= 2 (k = 2 keeps every edge).
+ * mask_out: m uint8 in edge-id order, 1 = in the k-truss (device or host).
+ * edges_out: host int64, number of edges in the k-truss; may be NULL.
+ * Errors: TC_EINVAL for k < 2.
+ */
+int ktruss(tc_graph* g, int32_t k, uint8_t* mask_out, int64_t* edges_out, void* cuda_stream);
+
+/*
+ * ktruss_max — truss decomposition (Section III-B): k = 3, 4, ... each level
+ * peeling the previous level's survivors, until none is left.
+ * kmax_out: host int32, the largest k with a non-empty k-truss (2 if the
+ * graph has edges but no triangle, 0 if it has no edge).
+ * truss_out: m int32 in edge-id order (device or host), the largest k whose
+ * k-truss contains the edge (>= 2); may be NULL.
+ * Synchronises the stream.
+ */
+int ktruss_max(tc_graph* g, int32_t* kmax_out, int32_t* truss_out, void* cuda_stream);
+
+/* Number of undirected edges after cleaning (m); -1 for a NULL graph. */
+int64_t tc_num_edges(const tc_graph* g);
+
+/* Number of vertices n given at build; -1 for a NULL graph. */
+int32_t tc_num_vertices(const tc_graph* g);
+
+/*
+ * tc_edges — the canonical edge list: lo[e] < hi[e] in original ids, in
+ * edge-id order.  lo, hi: m int32 each (device or host).
+ */
+int tc_edges(const tc_graph* g, int32_t* lo, int32_t* hi, void* cuda_stream);
+
+/*
+ * Sizes of a built graph, for reporting (the "edges" and "memory"
+ * performance metrics of Section IV) and for work estimates.
+ */
+typedef struct {
+    int64_t n;             /* vertices */
+    int64_t m_in;          /* input pairs given to tc_build_csr */
+    int64_t m;             /* undirected edges after cleaning */
+    int64_t max_degree;    /* largest vertex degree */
+    int64_t max_out;       /* largest out-degree |N+(u)| in the degree orientation */
+    int64_t wedge_work;    /* sum over oriented edges (u, v) of |N+(u)| + |N+(v)|:
+                              the list entries the masked product merges */
+    int64_t device_bytes;  /* device memory held by the graph */
+} tc_graph_info_t;
+
+/* Fills *info (host pointer).  Synchronises the stream. */
+int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream);
+
+/* Number of CUDA kernels the library has launched in this process (all
+ * graphs, all threads); lets a caller count the launches of a region. */
+int64_t tc_launch_count(void);
+
+/* Releases a graph (NULL is a no-op).  Synchronises the device's work on
+ * the graph's last stream first. */
+void tc_graph_free(tc_graph* g);
+
+/* Static description of a TC_* code. */
+const char* tc_strerror(int code);
+
+/* Description of the calling thread's most recent failed call ("" if none). */
+const char* tc_last_error(void);
+
+/*
+ * Test hook for host-side fault injection: the nth device allocation made
+ * by the library from now on (1 = the next one) fails as if the device were
+ * out of memory; 0 disables.  Returns the previous setting.
+ */
+int64_t tc_debug_fail_alloc(int64_t nth);
+
+/*
+ * Test hook: upper bound, in nanoseconds, on every device-side spin wait
+ * (default 2e9).  A wait that runs out makes the call return TC_ETIMEDOUT.
+ * Returns the previous value; values <= 0 leave it unchanged.
+ */
+int64_t tc_debug_spin_limit_ns(int64_t ns);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_GB300_H */

@@ -1,0 +1,295 @@
+"""Python binding of the GB300 triangle-counting / k-truss library.
+
+Thin ctypes marshalling over the C ABI in ``include/tc.h``: the functions
+here carry the ABI's names and do no computation of their own.  Every step
+of triangle counting, edge support and k-truss peeling runs in the CUDA
+kernels of ``libtc_gb300.so``; if that library is missing this module raises
+on first use instead of falling back to anything else.
+
+PyTorch supplies device buffers and streams: arrays are ``torch.Tensor``
+objects (CUDA or CPU) or numpy arrays (host); ``stream`` is a
+``torch.cuda.Stream`` (default: the current stream).
+
+Kernels of the Static Graph Challenge (Samsi et al. 2017):
+  * :func:`tc_count` — triangle count, Section III-A;
+  * :func:`tc_edge_support` — per-edge support, Algorithm 4's s = (R == 2) 1;
+  * :func:`ktruss` / :func:`ktruss_max` — k-truss and truss decomposition,
+    Section III-B.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "TCError", "Graph", "load_library", "library_path", "tc_build_csr", "tc_count",
+    "tc_edge_support", "ktruss", "ktruss_max", "tc_num_edges", "tc_num_vertices", "tc_edges", "tc_graph_info", "tc_launch_count",
+    "tc_graph_free", "tc_strerror", "tc_last_error", "tc_debug_fail_alloc",
+    "tc_debug_spin_limit_ns", "TC_OK", "TC_EINVAL", "TC_ERANGE", "TC_ENOMEM", "TC_ECUDA",
+    "TC_ETIMEDOUT", "TC_EOVERFLOW", "TC_INPUT_AUTO", "TC_INPUT_DEVICE", "TC_INPUT_HOST",
+]
+
+TC_OK, TC_EINVAL, TC_ERANGE, TC_ENOMEM, TC_ECUDA, TC_ETIMEDOUT, TC_EOVERFLOW = 0, -1, -2, -3, -4, -5, -6
+TC_INPUT_AUTO, TC_INPUT_DEVICE, TC_INPUT_HOST = 0, 1, 2
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Loads libtc_gb300.so (compiling it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"CUDA library not built: {_build.LIB}")
+        lib = ctypes.CDLL(_build.LIB)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        sig = {
+            "tc_build_csr": (ctypes.c_int, [vp, vp, i64, i32, ctypes.c_int, vp,
+                                            ctypes.POINTER(vp)]),
+            "tc_count": (ctypes.c_int, [vp, ctypes.POINTER(i64), vp]),
+            "tc_edge_support": (ctypes.c_int, [vp, vp, ctypes.POINTER(i64), vp]),
+            "ktruss": (ctypes.c_int, [vp, i32, vp, ctypes.POINTER(i64), vp]),
+            "ktruss_max": (ctypes.c_int, [vp, ctypes.POINTER(i32), vp, vp]),
+            "tc_num_edges": (i64, [vp]),
+            "tc_num_vertices": (i32, [vp]),
+            "tc_edges": (ctypes.c_int, [vp, vp, vp, vp]),
+            "tc_graph_free": (None, [vp]),
+            "tc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+            "tc_last_error": (ctypes.c_char_p, []),
+            "tc_graph_info": (ctypes.c_int, [vp, ctypes.POINTER(GraphInfo), vp]),
+            "tc_launch_count": (i64, []),
+            "tc_debug_fail_alloc": (i64, [i64]),
+            "tc_debug_spin_limit_ns": (i64, [i64]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+class GraphInfo(ctypes.Structure):
+    """Mirror of tc_graph_info_t."""
+    _fields_ = [(f, ctypes.c_int64) for f in
+                ("n", "m_in", "m", "max_degree", "max_out", "wedge_work", "device_bytes")]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class TCError(RuntimeError):
+    """A TC_E* status returned by the C ABI."""
+
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{message} (code {code})")
+        self.code = code
+
+
+def tc_strerror(code: int) -> str:
+    return load_library().tc_strerror(int(code)).decode()
+
+
+def tc_last_error() -> str:
+    return load_library().tc_last_error().decode()
+
+
+def _check(rc: int, what: str):
+    if rc != TC_OK:
+        raise TCError(rc, f"{what}: {tc_strerror(rc)}: {tc_last_error()}")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        if not torch.cuda.is_available():
+            return None
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _ptr(a):
+    """Raw address of a torch tensor or numpy array (must be contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return a.ctypes.data or None
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return a.data_ptr() or None
+
+
+class Graph:
+    """A device-resident graph built by :func:`tc_build_csr` (owned handle)."""
+
+    def __init__(self, handle: int, device):
+        self._h = handle
+        self.device = device
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("graph was freed")
+        return self._h
+
+    @property
+    def m(self) -> int:
+        return tc_num_edges(self)
+
+    @property
+    def n(self) -> int:
+        return tc_num_vertices(self)
+
+    def free(self):
+        if getattr(self, "_h", None):
+            load_library().tc_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _as_int32(a):
+    torch = _torch()
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.int32)
+    if a.dtype != torch.int32:
+        a = a.to(torch.int32)
+    return a.contiguous()
+
+
+def tc_build_csr(src, dst, n: int, stream=None, flags: int = TC_INPUT_AUTO) -> Graph:
+    """Cleans an edge list (Section II rules) and builds the device graph.
+
+    src, dst: int32 endpoints, 0-based, as CUDA or CPU tensors or numpy arrays.
+    """
+    lib = load_library()
+    torch = _torch()
+    src = _as_int32(src)
+    dst = _as_int32(dst)
+    if len(src) != len(dst):
+        raise ValueError("src and dst differ in length")
+    h = ctypes.c_void_p()
+    rc = lib.tc_build_csr(_ptr(src), _ptr(dst), len(src), int(n), int(flags),
+                          _stream_handle(stream), ctypes.byref(h))
+    _check(rc, "tc_build_csr")
+    return Graph(h.value, torch.device("cuda", torch.cuda.current_device()))
+
+
+def tc_count(g: Graph, stream=None) -> int:
+    """Number of triangles."""
+    out = ctypes.c_int64(0)
+    _check(load_library().tc_count(g.handle, ctypes.byref(out), _stream_handle(stream)),
+           "tc_count")
+    return out.value
+
+
+def tc_edge_support(g: Graph, out=None, stream=None, triangles: bool = True):
+    """Per-edge triangle support (int32, edge-id order) and the triangle count.
+
+    Returns (support, T); T is None when ``triangles`` is False.  ``out`` may
+    be a CUDA or CPU int32 tensor of m entries (allocated on the device if None).
+    """
+    torch = _torch()
+    m = g.m
+    if out is None:
+        out = torch.empty(m, dtype=torch.int32, device=g.device)
+    t = ctypes.c_int64(0)
+    rc = load_library().tc_edge_support(g.handle, _ptr(out), ctypes.byref(t) if triangles else None,
+                                        _stream_handle(stream))
+    _check(rc, "tc_edge_support")
+    return out, (t.value if triangles else None)
+
+
+def ktruss(g: Graph, k: int, out=None, stream=None):
+    """The k-truss as a uint8 mask over edge ids, and its edge count."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(g.m, dtype=torch.uint8, device=g.device)
+    left = ctypes.c_int64(0)
+    rc = load_library().ktruss(g.handle, int(k), _ptr(out), ctypes.byref(left),
+                               _stream_handle(stream))
+    _check(rc, "ktruss")
+    return out, left.value
+
+
+def ktruss_max(g: Graph, out=None, stream=None, want_truss: bool = True):
+    """Truss decomposition: (kmax, per-edge truss numbers or None)."""
+    torch = _torch()
+    if out is None and want_truss:
+        out = torch.empty(g.m, dtype=torch.int32, device=g.device)
+    kmax = ctypes.c_int32(0)
+    rc = load_library().ktruss_max(g.handle, ctypes.byref(kmax), _ptr(out) if want_truss else None,
+                                   _stream_handle(stream))
+    _check(rc, "ktruss_max")
+    return kmax.value, out
+
+
+def tc_num_edges(g: Graph) -> int:
+    return int(load_library().tc_num_edges(g.handle))
+
+
+def tc_num_vertices(g: Graph) -> int:
+    return int(load_library().tc_num_vertices(g.handle))
+
+
+def tc_edges(g: Graph, stream=None, device=None):
+    """The canonical edge list (lo, hi) in original ids, edge-id order."""
+    torch = _torch()
+    dev = g.device if device is None else device
+    lo = torch.empty(g.m, dtype=torch.int32, device=dev)
+    hi = torch.empty(g.m, dtype=torch.int32, device=dev)
+    _check(load_library().tc_edges(g.handle, _ptr(lo), _ptr(hi), _stream_handle(stream)),
+           "tc_edges")
+    return lo, hi
+
+
+def tc_graph_info(g: Graph, stream=None) -> dict:
+    """Sizes of the graph: n, m_in, m, max_degree, max_out, wedge_work, device_bytes."""
+    info = GraphInfo()
+    _check(load_library().tc_graph_info(g.handle, ctypes.byref(info), _stream_handle(stream)),
+           "tc_graph_info")
+    return info.as_dict()
+
+
+def tc_launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load_library().tc_launch_count())
+
+
+def tc_graph_free(g: Graph):
+    g.free()
+
+
+def tc_debug_fail_alloc(nth: int) -> int:
+    return int(load_library().tc_debug_fail_alloc(int(nth)))
+
+
+def tc_debug_spin_limit_ns(ns: int) -> int:
+    return int(load_library().tc_debug_spin_limit_ns(int(ns)))

@@ -1,0 +1,354 @@
+// build_csr.cu — device graph construction (Section II cleaning rules plus the
+// degree-ordered adjacency the triangle kernels use).
+//
+//   1. keys:   each input pair (u, v) -> packed (min << b | max); a self-loop
+//              gets a sentinel key that sorts last; ids outside [0, n) flag
+//              DEV_ERR_RANGE.                                    (Section II)
+//   2. sort + dedupe -> the canonical edge list lo[e] < hi[e].
+//   3. degrees, and the degree order rank(v) = position of (deg(v), v).
+//   4. both directions of every edge in rank ids, sorted -> a symmetric CSR
+//      whose rows are ascending; the part of row u above u is N+(u), the
+//      out-list of the degree-oriented adjacency L (Algorithm 3's L with a
+//      degree order in place of the index order).
+#include <algorithm>
+
+#include "tc_internal.cuh"
+
+namespace tc {
+namespace {
+
+constexpr int CB_THREADS = 256;
+constexpr int CB_ITEMS = 8;
+constexpr int CB_CHUNK = CB_THREADS * CB_ITEMS;
+
+__global__ void k_make_keys(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                            int64_t m_in, int32_t n, int bits, uint64_t sentinel,
+                            uint64_t* __restrict__ keys, int* __restrict__ err) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_in; i += stride) {
+        const int32_t u = src[i], v = dst[i];
+        uint64_t key = sentinel;
+        if (u < 0 || u >= n || v < 0 || v >= n) {
+            bad = true;
+        } else if (u != v) {
+            const uint64_t a = (uint64_t)min(u, v), b = (uint64_t)max(u, v);
+            key = (a << bits) | b;
+        }
+        keys[i] = key;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, DEV_ERR_RANGE);
+}
+
+// Stream compaction in index order: count per chunk, scan, write.
+struct DedupeOp {
+    const uint64_t* keys;
+    uint64_t sentinel;
+    int bits;
+    int32_t* lo;
+    int32_t* hi;
+    __device__ bool flag(int64_t i) const {
+        const uint64_t k = keys[i];
+        return k != sentinel && (i == 0 || keys[i - 1] != k);
+    }
+    __device__ void emit(int64_t i, int64_t pos) const {
+        const uint64_t k = keys[i];
+        lo[pos] = (int32_t)(k >> bits);
+        hi[pos] = (int32_t)(k & ((1ull << bits) - 1));
+    }
+};
+
+struct UpperOp {  // entries of the symmetric CSR that lie above their row
+    const uint64_t* keys;
+    const uint32_t* eid;
+    int bits;
+    int32_t* fwd;
+    __device__ bool flag(int64_t i) const {
+        const uint64_t k = keys[i];
+        return (k & ((1ull << bits) - 1)) > (k >> bits);
+    }
+    __device__ void emit(int64_t i, int64_t pos) const { fwd[pos] = (int32_t)eid[i]; }
+};
+
+template <typename Op>
+__global__ void __launch_bounds__(CB_THREADS) k_compact_count(Op op, int64_t n,
+                                                              uint32_t* __restrict__ totals) {
+    const int64_t base = (int64_t)blockIdx.x * CB_CHUNK;
+    uint32_t c = 0;
+#pragma unroll
+    for (int i = 0; i < CB_ITEMS; ++i) {
+        const int64_t idx = base + i * CB_THREADS + threadIdx.x;
+        if (idx < n && op.flag(idx)) ++c;
+    }
+    c = warp_sum(c);
+    __shared__ uint32_t s[CB_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < CB_THREADS / 32; ++w) t += s[w];
+        totals[blockIdx.x] = t;
+    }
+}
+
+template <typename Op>
+__global__ void __launch_bounds__(CB_THREADS) k_compact_write(Op op, int64_t n,
+                                                              const uint32_t* __restrict__ offs) {
+    __shared__ uint32_t s_scan[33];
+    const int64_t base = (int64_t)blockIdx.x * CB_CHUNK;
+    int64_t run = offs[blockIdx.x];
+#pragma unroll 1
+    for (int i = 0; i < CB_ITEMS; ++i) {
+        const int64_t idx = base + i * CB_THREADS + threadIdx.x;
+        const bool f = idx < n && op.flag(idx);
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(f ? 1u : 0u, s_scan, &tot);
+        if (f) op.emit(idx, run + ex);
+        run += tot;
+    }
+}
+
+// The chunk totals are uint32 and scanned as uint32: chunk offsets must stay
+// below 2^32, which holds because compaction inputs are below 2^32 entries.
+template <typename Op>
+int compact(const Op& op, int64_t n, int64_t* count_out, uint64_t* scalar_dev, cudaStream_t s) {
+    if (n == 0) {
+        *count_out = 0;
+        return TC_OK;
+    }
+    if (n >= (1ll << 32)) return fail(TC_EOVERFLOW, "compaction input of 2^32 or more entries");
+    const int64_t chunks = (n + CB_CHUNK - 1) / CB_CHUNK;
+    Scratch sc(s);
+    uint32_t* totals;
+    TC_TRY(sc.alloc(&totals, chunks));
+    k_compact_count<Op><<<(unsigned)chunks, CB_THREADS, 0, s>>>(op, n, totals);
+    TC_LAUNCH_CHECK("k_compact_count");
+    TC_TRY(scan_block_totals(totals, chunks, scalar_dev, s));
+    k_compact_write<Op><<<(unsigned)chunks, CB_THREADS, 0, s>>>(op, n, totals);
+    TC_LAUNCH_CHECK("k_compact_write");
+    uint64_t cnt = 0;
+    TC_CUDA_TRY(cudaMemcpyAsync(&cnt, scalar_dev, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    TC_CUDA_TRY(cudaStreamSynchronize(s));
+    *count_out = (int64_t)cnt;
+    return TC_OK;
+}
+
+__global__ void k_degree(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                         int64_t m, int32_t* __restrict__ deg) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        atomicAdd(&deg[lo[e]], 1);
+        atomicAdd(&deg[hi[e]], 1);
+    }
+}
+
+__global__ void k_vertex_keys(const int32_t* __restrict__ deg, int32_t n, int bits,
+                              uint64_t* __restrict__ keys) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        keys[v] = ((uint64_t)deg[v] << bits) | (uint64_t)v;
+}
+
+__global__ void k_rank(const uint64_t* __restrict__ sorted, int32_t n, int bits,
+                       int32_t* __restrict__ rank) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t mask = (1ull << bits) - 1;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
+        rank[sorted[p] & mask] = (int32_t)p;
+}
+
+__global__ void k_pairs(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi, int64_t m,
+                        const int32_t* __restrict__ rank, int bits, int2* __restrict__ ends,
+                        uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int32_t a = rank[lo[e]], c = rank[hi[e]];
+        const int32_t u = min(a, c), v = max(a, c);
+        ends[e] = make_int2(u, v);
+        keys[2 * e] = ((uint64_t)u << bits) | (uint64_t)v;
+        keys[2 * e + 1] = ((uint64_t)v << bits) | (uint64_t)u;
+        vals[2 * e] = (uint32_t)e;
+        vals[2 * e + 1] = (uint32_t)e;
+    }
+}
+
+// col from the sorted keys; row boundaries -> rowptr; first entry above the
+// row -> upper (rows with none keep upper = rowptr[r + 1], set beforehand).
+__global__ void k_csr_fill(const uint64_t* __restrict__ keys, int64_t nnz, int32_t n, int bits,
+                           int32_t* __restrict__ col, int64_t* __restrict__ rowptr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t mask = (1ull << bits) - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= nnz; i += stride) {
+        const int64_t r_prev = i == 0 ? -1 : (int64_t)(keys[i - 1] >> bits);
+        const int64_t r_cur = i == nnz ? (int64_t)n : (int64_t)(keys[i] >> bits);
+        if (i < nnz) col[i] = (int32_t)(keys[i] & mask);
+        for (int64_t r = r_prev + 1; r <= r_cur; ++r) rowptr[r] = i;
+    }
+}
+
+__global__ void k_upper_init(const int64_t* __restrict__ rowptr, int32_t n,
+                             int64_t* __restrict__ upper) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride)
+        upper[r] = rowptr[r + 1];
+}
+
+__global__ void k_upper(const uint64_t* __restrict__ keys, int64_t nnz, int bits,
+                        int64_t* __restrict__ upper) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t mask = (1ull << bits) - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += stride) {
+        const uint64_t k = keys[i];
+        const uint64_t row = k >> bits, c = k & mask;
+        if (c > row) {
+            const bool first = i == 0 || (keys[i - 1] >> bits) != row ||
+                                (keys[i - 1] & mask) < row;
+            if (first) upper[row] = i;
+        }
+    }
+}
+
+__global__ void k_row_stats(const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
+                            int32_t n, unsigned long long* __restrict__ out /* [0]=maxdeg [1]=maxout */) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long md = 0, mo = 0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        md = max(md, (unsigned long long)(rowptr[r + 1] - rowptr[r]));
+        mo = max(mo, (unsigned long long)(rowptr[r + 1] - upper[r]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        md = max(md, __shfl_xor_sync(0xffffffffu, md, o));
+        mo = max(mo, __shfl_xor_sync(0xffffffffu, mo, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&out[0], md);
+        atomicMax(&out[1], mo);
+    }
+}
+
+inline unsigned grid_for(int64_t n, int threads = 256) {
+    const int64_t cap = (int64_t)num_sms() * 32;
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    return (unsigned)std::min(b, cap);
+}
+
+}  // namespace
+
+int build_graph(Graph* g, const int32_t* src, const int32_t* dst, cudaStream_t s) {
+    const int64_t m_in = g->m_in;
+    const int32_t n = g->n;
+    const int bits = bits_for((uint64_t)(n > 1 ? n - 1 : 1));
+    g->bits = bits;
+    const uint64_t id_mask = (1ull << bits) - 1;
+    const uint64_t sentinel = (id_mask << bits) | id_mask;
+    uint64_t* scalar = reinterpret_cast<uint64_t*>(g->dev_scalars);
+
+    TC_CUDA_TRY(cudaMemsetAsync(g->dev_err, 0, sizeof(int), s));
+    int64_t m = 0;
+    {
+        // 1-2. canonical edge list
+        Scratch sc(s);
+        uint64_t *keys = nullptr, *keys_alt = nullptr;
+        TC_TRY(sc.alloc(&keys, m_in));
+        if (m_in > 0) {
+            k_make_keys<<<grid_for(m_in), 256, 0, s>>>(src, dst, m_in, n, bits, sentinel, keys,
+                                                      g->dev_err);
+            TC_LAUNCH_CHECK("k_make_keys");
+            TC_TRY(check_dev_err(g->dev_err, s));
+            TC_TRY(sc.alloc(&keys_alt, m_in));
+            TC_TRY(radix_sort_u64(keys, keys_alt, nullptr, nullptr, m_in, 2 * bits, g->dev_err, s));
+        }
+        // upper bound for the unique count is m_in; allocate after counting
+        DedupeOp op{keys, sentinel, bits, nullptr, nullptr};
+        const int64_t chunks = (m_in + CB_CHUNK - 1) / CB_CHUNK;
+        if (m_in > 0) {
+            uint32_t* totals;
+            TC_TRY(sc.alloc(&totals, chunks));
+            k_compact_count<DedupeOp><<<(unsigned)chunks, CB_THREADS, 0, s>>>(op, m_in, totals);
+            TC_LAUNCH_CHECK("k_compact_count");
+            TC_TRY(scan_block_totals(totals, chunks, scalar, s));
+            uint64_t cnt = 0;
+            TC_CUDA_TRY(cudaMemcpyAsync(&cnt, scalar, 8, cudaMemcpyDeviceToHost, s));
+            TC_CUDA_TRY(cudaStreamSynchronize(s));
+            TC_TRY(check_dev_err(g->dev_err, s));
+            m = (int64_t)cnt;
+            if (m > 0x7fffffffLL) return fail(TC_EOVERFLOW, "more than 2^31-1 edges after cleaning");
+            TC_TRY(dev_alloc_n(&g->lo, m, s));
+            TC_TRY(dev_alloc_n(&g->hi, m, s));
+            op.lo = g->lo;
+            op.hi = g->hi;
+            k_compact_write<DedupeOp><<<(unsigned)chunks, CB_THREADS, 0, s>>>(op, m_in, totals);
+            TC_LAUNCH_CHECK("k_compact_write");
+        } else {
+            TC_TRY(dev_alloc_n(&g->lo, 0, s));
+            TC_TRY(dev_alloc_n(&g->hi, 0, s));
+        }
+    }
+    g->m = m;
+
+    // 3-4. degree order and the symmetric CSR in rank ids
+    TC_TRY(dev_alloc_n(&g->rowptr, (int64_t)n + 1, s));
+    TC_TRY(dev_alloc_n(&g->upper, (int64_t)n, s));
+    TC_TRY(dev_alloc_n(&g->ends, m, s));
+    TC_TRY(dev_alloc_n(&g->col, 2 * m, s));
+    TC_TRY(dev_alloc_n(&g->eid, 2 * m, s));
+    TC_TRY(dev_alloc_n(&g->fwd, m, s));
+    {
+        Scratch sc(s);
+        int32_t *deg, *rank;
+        uint64_t *vkeys, *vkeys_alt;
+        TC_TRY(sc.alloc(&deg, n));
+        TC_TRY(sc.alloc(&rank, n));
+        TC_TRY(sc.alloc(&vkeys, n));
+        TC_TRY(sc.alloc(&vkeys_alt, n));
+        TC_CUDA_TRY(cudaMemsetAsync(deg, 0, sizeof(int32_t) * n, s));
+        if (m > 0) {
+            k_degree<<<grid_for(m), 256, 0, s>>>(g->lo, g->hi, m, deg);
+            TC_LAUNCH_CHECK("k_degree");
+        }
+        k_vertex_keys<<<grid_for(n), 256, 0, s>>>(deg, n, bits, vkeys);
+        TC_LAUNCH_CHECK("k_vertex_keys");
+        TC_TRY(radix_sort_u64(vkeys, vkeys_alt, nullptr, nullptr, n, 2 * bits, g->dev_err, s));
+        k_rank<<<grid_for(n), 256, 0, s>>>(vkeys, n, bits, rank);
+        TC_LAUNCH_CHECK("k_rank");
+
+        const int64_t nnz = 2 * m;
+        uint64_t *pkeys, *pkeys_alt;
+        uint32_t *pvals, *pvals_alt;
+        TC_TRY(sc.alloc(&pkeys, nnz));
+        TC_TRY(sc.alloc(&pkeys_alt, nnz));
+        TC_TRY(sc.alloc(&pvals_alt, nnz));
+        pvals = reinterpret_cast<uint32_t*>(g->eid);
+        if (m > 0) {
+            k_pairs<<<grid_for(m), 256, 0, s>>>(g->lo, g->hi, m, rank, bits, g->ends, pkeys, pvals);
+            TC_LAUNCH_CHECK("k_pairs");
+            TC_TRY(radix_sort_u64(pkeys, pkeys_alt, pvals, pvals_alt, nnz, 2 * bits, g->dev_err, s));
+        }
+        k_csr_fill<<<grid_for(nnz + 1), 256, 0, s>>>(pkeys, nnz, n, bits, g->col, g->rowptr);
+        TC_LAUNCH_CHECK("k_csr_fill");
+        k_upper_init<<<grid_for(n), 256, 0, s>>>(g->rowptr, n, g->upper);
+        TC_LAUNCH_CHECK("k_upper_init");
+        if (m > 0) {
+            k_upper<<<grid_for(nnz), 256, 0, s>>>(pkeys, nnz, bits, g->upper);
+            TC_LAUNCH_CHECK("k_upper");
+            int64_t cnt = 0;
+            UpperOp up{pkeys, pvals, bits, g->fwd};
+            TC_TRY(compact(up, nnz, &cnt, scalar, s));
+            if (cnt != m) return fail(TC_ECUDA, "internal: oriented edge count mismatch");
+        }
+        TC_CUDA_TRY(cudaMemsetAsync(g->dev_scalars, 0, 2 * sizeof(unsigned long long), s));
+        k_row_stats<<<grid_for(n), 256, 0, s>>>(g->rowptr, g->upper, n, g->dev_scalars);
+        TC_LAUNCH_CHECK("k_row_stats");
+        unsigned long long st[2];
+        TC_CUDA_TRY(cudaMemcpyAsync(st, g->dev_scalars, sizeof(st), cudaMemcpyDeviceToHost, s));
+        TC_CUDA_TRY(cudaStreamSynchronize(s));
+        g->max_deg = (int32_t)st[0];
+        g->max_out = (int32_t)st[1];
+        TC_TRY(check_dev_err(g->dev_err, s));
+    }
+    return TC_OK;
+}
+
+}  // namespace tc

@@ -1,0 +1,322 @@
+// tc_abi.cu — the extern "C" entry points declared in include/tc.h: argument
+// checks, host/device marshalling of caller buffers, the graph object, error
+// reporting, and the library's stream-ordered device allocator.
+#include <atomic>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "tc_internal.cuh"
+
+struct tc_graph {
+    tc::Graph g;
+};
+
+namespace tc {
+
+namespace {
+thread_local std::string t_last_error;
+std::atomic<int64_t> g_fail_alloc{0};
+std::atomic<int64_t> g_spin_ns{2000000000LL};
+std::atomic<int64_t> g_launches{0};
+}  // namespace
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int fail(int code, const std::string& what) {
+    t_last_error = what;
+    return code;
+}
+
+int64_t spin_limit_ns() { return g_spin_ns.load(); }
+
+int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    int64_t c = g_fail_alloc.load();
+    while (c > 0) {
+        if (g_fail_alloc.compare_exchange_weak(c, c - 1)) {
+            if (c == 1) return fail(TC_ENOMEM, "injected device allocation failure");
+            break;
+        }
+    }
+    const cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? TC_ENOMEM : TC_ECUDA,
+                    std::string("cudaMallocAsync(") + std::to_string(bytes) +
+                        " bytes): " + cudaGetErrorString(e));
+    }
+    return TC_OK;
+}
+
+void dev_free(void* p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+bool is_host_pointer(const void* p) {
+    cudaPointerAttributes a;
+    const cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeUnregistered || a.type == cudaMemoryTypeHost;
+}
+
+int check_dev_err(int* dev_err, cudaStream_t s) {
+    int h = 0;
+    TC_CUDA_TRY(cudaMemcpyAsync(&h, dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h == 0) return TC_OK;
+    TC_CUDA_TRY(cudaMemsetAsync(dev_err, 0, sizeof(int), s));
+    if (h & DEV_ERR_RANGE) return fail(TC_ERANGE, "vertex id outside [0, n)");
+    if (h & DEV_ERR_TIMEOUT) return fail(TC_ETIMEDOUT, "a device-side wait ran out of time");
+    return fail(TC_ECUDA, "internal device bounds check failed");
+}
+
+void free_graph(Graph* g) {
+    cudaStream_t s = g->last_stream;
+    dev_free(g->lo, s);
+    dev_free(g->hi, s);
+    dev_free(g->ends, s);
+    dev_free(g->rowptr, s);
+    dev_free(g->upper, s);
+    dev_free(g->col, s);
+    dev_free(g->eid, s);
+    dev_free(g->fwd, s);
+    dev_free(g->support, s);
+    dev_free(g->dev_err, s);
+    dev_free(g->dev_scalars, s);
+    cudaStreamSynchronize(s);
+}
+
+}  // namespace tc
+
+namespace {
+
+using tc::fail;
+
+struct DeviceGuard {  // makes `dev` current for the scope of a call
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+inline cudaStream_t as_stream(void* p) { return reinterpret_cast<cudaStream_t>(p); }
+
+// Writes `count` elements of device array `src` to the caller's buffer `dst`
+// (device or host).  Host destinations synchronise the stream.
+template <typename T>
+int deliver(T* dst, const T* src, int64_t count, cudaStream_t s) {
+    if (count <= 0) return TC_OK;
+    const bool host = tc::is_host_pointer(dst);
+    TC_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(T) * count,
+                                host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    if (host) TC_CUDA_TRY(cudaStreamSynchronize(s));
+    return TC_OK;
+}
+
+int begin_call(tc_graph* g, void* stream) {
+    if (!g) return fail(TC_EINVAL, "graph is NULL");
+    g->g.last_stream = as_stream(stream);
+    return TC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tc_build_csr(const int32_t* src, const int32_t* dst, int64_t m_in, int32_t n, int flags,
+                 void* cuda_stream, tc_graph** out) {
+    if (!out) return fail(TC_EINVAL, "out is NULL");
+    if (n < 1) return fail(TC_EINVAL, "n must be >= 1");
+    if (m_in < 0) return fail(TC_EINVAL, "m_in must be >= 0");
+    if (m_in > 0 && (!src || !dst)) return fail(TC_EINVAL, "src/dst is NULL");
+    if (flags != TC_INPUT_AUTO && flags != TC_INPUT_DEVICE && flags != TC_INPUT_HOST)
+        return fail(TC_EINVAL, "unknown flags");
+    if (m_in >= (1ll << 32)) return fail(TC_EOVERFLOW, "m_in must be below 2^32");
+    cudaStream_t s = as_stream(cuda_stream);
+    int dev = 0;
+    TC_CUDA_TRY(cudaGetDevice(&dev));
+
+    bool host = flags == TC_INPUT_HOST;
+    if (flags == TC_INPUT_AUTO && m_in > 0) host = tc::is_host_pointer(src) || tc::is_host_pointer(dst);
+
+    tc_graph* h = new (std::nothrow) tc_graph();
+    if (!h) return fail(TC_ENOMEM, "host allocation of the graph");
+    tc::Graph* g = &h->g;
+    g->device = dev;
+    g->n = n;
+    g->m_in = m_in;
+    g->last_stream = s;
+    int rc = tc::dev_alloc_n(&g->dev_err, 1, s);
+    if (rc == TC_OK) rc = tc::dev_alloc_n(&g->dev_scalars, 8, s);
+    if (rc == TC_OK) {
+        const int32_t* sd = src;
+        const int32_t* dd = dst;
+        tc::Scratch sc(s);
+        if (host && m_in > 0) {
+            int32_t *s2 = nullptr, *d2 = nullptr;
+            rc = sc.alloc(&s2, m_in);
+            if (rc == TC_OK) rc = sc.alloc(&d2, m_in);
+            if (rc == TC_OK) {
+                cudaError_t e = cudaMemcpyAsync(s2, src, sizeof(int32_t) * m_in,
+                                                cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(d2, dst, sizeof(int32_t) * m_in, cudaMemcpyHostToDevice, s);
+                if (e != cudaSuccess)
+                    rc = fail(TC_ECUDA, std::string("input copy: ") + cudaGetErrorString(e));
+            }
+            sd = s2;
+            dd = d2;
+        }
+        if (rc == TC_OK) rc = tc::build_graph(g, sd, dd, s);
+    }
+    if (rc != TC_OK) {
+        tc::free_graph(g);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return TC_OK;
+}
+
+int tc_count(tc_graph* g, int64_t* triangles_out, void* cuda_stream) {
+    TC_TRY(begin_call(g, cuda_stream));
+    if (!triangles_out) return fail(TC_EINVAL, "triangles_out is NULL");
+    DeviceGuard dg(g->g.device);
+    int64_t T = 0;
+    TC_TRY(tc::compute_support(&g->g, nullptr, false, &T, as_stream(cuda_stream)));
+    g->g.triangles = T;
+    *triangles_out = T;
+    return TC_OK;
+}
+
+int tc_edge_support(tc_graph* g, int32_t* support_out, int64_t* triangles_out,
+                    void* cuda_stream) {
+    TC_TRY(begin_call(g, cuda_stream));
+    tc::Graph* gg = &g->g;
+    if (!support_out && gg->m > 0) return fail(TC_EINVAL, "support_out is NULL");
+    DeviceGuard dg(gg->device);
+    cudaStream_t s = as_stream(cuda_stream);
+    if (!gg->support) TC_TRY(tc::dev_alloc_n(&gg->support, gg->m, s));
+    gg->support_valid = false;
+    int64_t T = 0;
+    TC_TRY(tc::compute_support(gg, gg->support, true, triangles_out ? &T : nullptr, s));
+    gg->support_valid = true;
+    if (triangles_out) {
+        gg->triangles = T;
+        *triangles_out = T;
+    }
+    return deliver(support_out, gg->support, gg->m, s);
+}
+
+int ktruss(tc_graph* g, int32_t k, uint8_t* mask_out, int64_t* edges_out, void* cuda_stream) {
+    TC_TRY(begin_call(g, cuda_stream));
+    if (k < 2) return fail(TC_EINVAL, "k must be >= 2");
+    tc::Graph* gg = &g->g;
+    if (!mask_out && gg->m > 0) return fail(TC_EINVAL, "mask_out is NULL");
+    DeviceGuard dg(gg->device);
+    cudaStream_t s = as_stream(cuda_stream);
+    const bool host = gg->m > 0 && tc::is_host_pointer(mask_out);
+    tc::Scratch sc(s);
+    uint8_t* mask = mask_out;
+    if (host) TC_TRY(sc.alloc(&mask, gg->m));
+    int64_t left = 0;
+    TC_TRY(tc::peel_ktruss(gg, k, mask, &left, s));
+    if (host) TC_TRY(deliver(mask_out, mask, gg->m, s));
+    if (edges_out) *edges_out = left;
+    return tc::check_dev_err(gg->dev_err, s);
+}
+
+int ktruss_max(tc_graph* g, int32_t* kmax_out, int32_t* truss_out, void* cuda_stream) {
+    TC_TRY(begin_call(g, cuda_stream));
+    if (!kmax_out) return fail(TC_EINVAL, "kmax_out is NULL");
+    tc::Graph* gg = &g->g;
+    DeviceGuard dg(gg->device);
+    cudaStream_t s = as_stream(cuda_stream);
+    tc::Scratch sc(s);
+    int32_t* truss = truss_out;
+    const bool direct = truss_out && gg->m > 0 && !tc::is_host_pointer(truss_out);
+    if (!direct) TC_TRY(sc.alloc(&truss, gg->m));
+    int32_t kmax = 0;
+    TC_TRY(tc::peel_decompose(gg, truss, &kmax, s));
+    if (truss_out && !direct) TC_TRY(deliver(truss_out, truss, gg->m, s));
+    TC_TRY(tc::check_dev_err(gg->dev_err, s));
+    *kmax_out = kmax;
+    return TC_OK;
+}
+
+int64_t tc_num_edges(const tc_graph* g) { return g ? g->g.m : -1; }
+
+int32_t tc_num_vertices(const tc_graph* g) { return g ? g->g.n : -1; }
+
+int tc_edges(const tc_graph* g, int32_t* lo, int32_t* hi, void* cuda_stream) {
+    if (!g) return fail(TC_EINVAL, "graph is NULL");
+    if (g->g.m > 0 && (!lo || !hi)) return fail(TC_EINVAL, "lo/hi is NULL");
+    DeviceGuard dg(g->g.device);
+    cudaStream_t s = as_stream(cuda_stream);
+    TC_TRY(deliver(lo, g->g.lo, g->g.m, s));
+    return deliver(hi, g->g.hi, g->g.m, s);
+}
+
+int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream) {
+    if (!g || !info) return fail(TC_EINVAL, "graph or info is NULL");
+    tc::Graph* gg = const_cast<tc::Graph*>(&g->g);
+    DeviceGuard dg(gg->device);
+    int64_t ww = 0;
+    TC_TRY(tc::graph_wedge_work(gg, &ww, as_stream(cuda_stream)));
+    info->n = gg->n;
+    info->m_in = gg->m_in;
+    info->m = gg->m;
+    info->max_degree = gg->max_deg;
+    info->max_out = gg->max_out;
+    info->wedge_work = ww;
+    const int64_t m = gg->m, n = gg->n;
+    info->device_bytes = m * (4 + 4 + 8 + 4 + 4 + 4) + 8 * (n + 1) + 8 * n +
+                         (gg->support ? 4 * m : 0);
+    return TC_OK;
+}
+
+int64_t tc_launch_count(void) { return tc::g_launches.load(); }
+
+void tc_graph_free(tc_graph* g) {
+    if (!g) return;
+    {
+        DeviceGuard dg(g->g.device);
+        tc::free_graph(&g->g);
+    }
+    delete g;
+}
+
+const char* tc_strerror(int code) {
+    switch (code) {
+        case TC_OK: return "ok";
+        case TC_EINVAL: return "invalid argument";
+        case TC_ERANGE: return "vertex id out of range";
+        case TC_ENOMEM: return "out of memory";
+        case TC_ECUDA: return "CUDA error";
+        case TC_ETIMEDOUT: return "device-side wait timed out";
+        case TC_EOVERFLOW: return "size overflow";
+        default: return "unknown error";
+    }
+}
+
+const char* tc_last_error(void) { return tc::t_last_error.c_str(); }
+
+int64_t tc_debug_fail_alloc(int64_t nth) { return tc::g_fail_alloc.exchange(nth < 0 ? 0 : nth); }
+
+int64_t tc_debug_spin_limit_ns(int64_t ns) {
+    if (ns <= 0) return tc::g_spin_ns.load();
+    return tc::g_spin_ns.exchange(ns);
+}
+
+}  // extern "C"

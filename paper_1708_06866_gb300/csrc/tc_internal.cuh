@@ -1,0 +1,217 @@
+// tc_internal.cuh — shared declarations of the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/tc.h"
+
+namespace tc {
+
+// ---------------------------------------------------------------- errors
+
+// Records a failure for tc_last_error() and returns `code`.
+int fail(int code, const std::string& what);
+
+#define TC_CUDA_TRY(expr)                                                              \
+    do {                                                                               \
+        cudaError_t err__ = (expr);                                                    \
+        if (err__ != cudaSuccess)                                                      \
+            return ::tc::fail(err__ == cudaErrorMemoryAllocation ? TC_ENOMEM : TC_ECUDA, \
+                              std::string(#expr) + ": " + cudaGetErrorString(err__));  \
+    } while (0)
+
+#define TC_TRY(expr)                 \
+    do {                             \
+        int rc__ = (expr);           \
+        if (rc__ != TC_OK) return rc__; \
+    } while (0)
+
+// Every kernel launch is followed by this check, which also counts it.
+void count_launch();
+#define TC_LAUNCH_CHECK(name)            \
+    do {                                 \
+        ::tc::count_launch();            \
+        TC_CUDA_TRY(cudaGetLastError()); \
+    } while (0)
+
+// Device-side error word: kernels OR these bits into it, the host maps them.
+enum : int {
+    DEV_ERR_RANGE = 1,     // vertex id outside [0, n)
+    DEV_ERR_TIMEOUT = 2,   // a bounded spin wait gave up
+    DEV_ERR_BOUNDS = 4,    // an internal index check failed (a library bug)
+};
+
+int64_t spin_limit_ns();
+
+// ---------------------------------------------------------------- memory
+
+// Stream-ordered device allocation with the fault-injection hook.
+int dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+
+template <typename T>
+int dev_alloc_n(T** p, int64_t count, cudaStream_t s) {
+    return dev_alloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)(count > 0 ? count : 1), s);
+}
+
+// RAII holder for scratch buffers freed (stream-ordered) at scope exit.
+struct Scratch {
+    cudaStream_t s;
+    void* ptrs[32];
+    int n = 0;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    template <typename T>
+    int alloc(T** p, int64_t count) {
+        int rc = dev_alloc_n(p, count, s);
+        if (rc == TC_OK) ptrs[n++] = *p;
+        return rc;
+    }
+    ~Scratch() {
+        for (int i = 0; i < n; ++i) dev_free(ptrs[i], s);
+    }
+};
+
+// Pointer location: true if `p` is host memory the device cannot address
+// directly as device memory (pageable, or pinned/registered host memory).
+bool is_host_pointer(const void* p);
+
+// ---------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide exclusive scan of one uint32 per thread (blockDim.x <= 1024,
+// a multiple of 32).  `sh` must hold 33 entries of shared memory.  Returns the
+// exclusive prefix; *total receives the block sum.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* sh,
+                                                         uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t = lane < nwarps ? sh[lane] : 0u;
+        uint32_t tt = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, tt, o);
+            if (lane >= o) tt += y;
+        }
+        if (lane < nwarps) sh[lane] = tt - t;
+        if (lane == 31) sh[32] = tt;
+    }
+    __syncthreads();
+    const uint32_t res = sh[warp] + x - v;
+    *total = sh[32];
+    __syncthreads();
+    return res;
+}
+
+inline int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+inline int bits_for(uint64_t maxval) {  // bits needed to hold values 0..maxval (>= 1)
+    int b = 1;
+    while (b < 64 && (maxval >> b) != 0) ++b;
+    return b;
+}
+
+// ---------------------------------------------------------------- primitives
+
+// LSD radix sort of uint64 keys on bits [0, key_bits), stable, optionally
+// carrying uint32 values.  keys/vals are sorted in place (alt buffers are
+// scratch of the same size, provided by the caller).  vals may be NULL.
+int radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
+                   int64_t n, int key_bits, int* dev_err, cudaStream_t s);
+
+// Exclusive scan of `count` uint32 block totals in place (one kernel).
+int scan_block_totals(uint32_t* totals, int64_t count, uint64_t* grand_total_dev,
+                      cudaStream_t s);
+
+// Reads the device error word, maps it to a TC code, clears it.
+int check_dev_err(int* dev_err, cudaStream_t s);
+
+// ---------------------------------------------------------------- the graph
+
+struct Graph {
+    int device = 0;
+    int32_t n = 0;
+    int64_t m_in = 0;
+    int64_t m = 0;       // undirected edges after cleaning
+    int bits = 1;        // bits per vertex id in packed keys
+    // canonical edge list (original ids), edge-id order
+    int32_t* lo = nullptr;
+    int32_t* hi = nullptr;
+    // endpoints in rank ids, (min, max), edge-id order
+    int2* ends = nullptr;
+    // symmetric CSR over rank ids: row r = [rowptr[r], rowptr[r+1]); its part
+    // above r (the oriented out-list N+(r)) starts at upper[r]
+    int64_t* rowptr = nullptr;
+    int64_t* upper = nullptr;
+    int32_t* col = nullptr;   // 2m neighbour rank ids
+    int32_t* eid = nullptr;   // 2m edge ids
+    int32_t* fwd = nullptr;   // m edge ids in oriented (u, v) order
+    int32_t max_out = 0;      // max |N+(u)|
+    int32_t max_deg = 0;
+    int64_t wedge_work = -1;  // sum of |N+(u)| + |N+(v)| over oriented edges (lazy)
+    // cached support (edge-id order) and triangle count
+    int32_t* support = nullptr;
+    bool support_valid = false;
+    int64_t triangles = -1;
+    int* dev_err = nullptr;
+    unsigned long long* dev_scalars = nullptr;  // small device scratch (8 words)
+    cudaStream_t last_stream = nullptr;
+};
+
+int build_graph(Graph* g, const int32_t* src_d, const int32_t* dst_d, cudaStream_t s);
+void free_graph(Graph* g);
+int compute_support(Graph* g, int32_t* s_out_dev, bool want_support, int64_t* triangles,
+                    cudaStream_t s);
+int peel_ktruss(Graph* g, int32_t k, uint8_t* mask_dev, int64_t* edges_left, cudaStream_t s);
+int graph_wedge_work(Graph* g, int64_t* out, cudaStream_t s);
+int peel_decompose(Graph* g, int32_t* truss_dev, int32_t* kmax, cudaStream_t s);
+
+}  // namespace tc

@@ -1,0 +1,65 @@
+"""Writes stored oracle results for workloads too large to re-run in the GPU tests.
+
+Calls only the oracle (and the seeded generators that feed it).  Usage:
+    python tests/golden/make_oracle_fixtures.py rmat20 [--truss]
+writes tests/golden/<name>_oracle.txt.  Hashes are SHA-256 of the little-endian
+int32 arrays in canonical edge order.
+"""
+import argparse
+import hashlib
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import graphgen  # noqa: E402
+import oracle  # noqa: E402
+
+
+def sha(a: np.ndarray) -> str:
+    return hashlib.sha256(np.ascontiguousarray(a, dtype="<i4").tobytes()).hexdigest()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workload")
+    ap.add_argument("--truss", action="store_true", help="also the full truss decomposition")
+    ap.add_argument("--ks", default="", help="comma-separated k values for single k-truss runs")
+    args = ap.parse_args()
+    w = graphgen.WORKLOADS[args.workload]
+    s, d, n = w.generate()
+    lines = [f"# oracle results for workload {w.name}: {w.description}",
+             "# written by tests/golden/make_oracle_fixtures.py (oracle only)"]
+    t0 = time.time()
+    g = oracle.OracleGraph.from_edges(s, d, n)
+    lines.append(f"n {n}")
+    lines.append(f"m_in {len(s)}")
+    lines.append(f"m {g.m}")
+    lines.append(f"lo_hi_sha256 {sha(g.lo)} {sha(g.hi)}")
+    T = g.count()
+    lines.append(f"triangles {T}")
+    sup = g.support()
+    lines.append(f"support_sha256 {sha(sup)}")
+    lines.append(f"support_sum {int(sup.sum(dtype=np.int64))}")
+    for k in [int(x) for x in args.ks.split(",") if x]:
+        mask, _, left = g.ktruss(k)
+        lines.append(f"ktruss {k} {left} {sha(mask.astype(np.int32))}")
+    if args.truss:
+        kmax, t = g.truss_decomposition()
+        lines.append(f"kmax {kmax}")
+        lines.append(f"truss_sha256 {sha(t)}")
+        counts = [int((t >= k).sum()) for k in range(2, kmax + 2)]
+        lines.append("truss_edges_from_k2 " + " ".join(map(str, counts)))
+    lines.append(f"# oracle wall time {time.time() - t0:.1f} s")
+    out = os.path.join(HERE, f"{w.name}_oracle.txt")
+    with open(out, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    print(out)
+
+
+if __name__ == "__main__":
+    main()

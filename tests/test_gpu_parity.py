@@ -1,0 +1,263 @@
+"""GPU parity: every C-ABI call against the CPU oracle, bit-exact.
+
+All outputs are integers (int64 triangle counts, int32 supports and truss
+numbers, uint8 masks, int32 canonical edge lists), so the bar is equality.
+Inputs are seeded synthetic graphs: the paper's examples, closed-form
+families, Erdős–Rényi and R-MAT graphs at sizes that span many radix-sort
+tiles and compaction chunks with ragged tails, edge lists with self-loops,
+repeats and reversed pairs, and the degenerate cases (no edges, one vertex,
+a maximum-degree star).
+"""
+import hashlib
+import os
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from conftest import ROOT, read_fixture
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machines too
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1708_06866_gb300 as tc  # noqa: E402
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
+
+
+def gpu_all(src, dst, n, ks=(2, 3, 4, 5, 6)):
+    g = tc.tc_build_csr(dev(src), dev(dst), n)
+    lo, hi = tc.tc_edges(g)
+    T = tc.tc_count(g)
+    s, T2 = tc.tc_edge_support(g)
+    masks = {k: tc.ktruss(g, k) for k in ks}
+    kmax, truss = tc.ktruss_max(g)
+    out = dict(m=g.m, lo=lo.cpu().numpy(), hi=hi.cpu().numpy(), T=T, T2=T2,
+               s=s.cpu().numpy(), masks={k: (mk.cpu().numpy(), c) for k, (mk, c) in masks.items()},
+               kmax=kmax, truss=truss.cpu().numpy())
+    tc.tc_graph_free(g)
+    return out
+
+
+def check(src, dst, n, ks=(2, 3, 4, 5, 6)):
+    got = gpu_all(src, dst, n, ks)
+    og = oracle.OracleGraph.from_edges(src, dst, n)
+    assert got["m"] == og.m
+    assert np.array_equal(got["lo"], og.lo) and np.array_equal(got["hi"], og.hi)
+    T = og.count()
+    assert got["T"] == T and got["T2"] == T
+    assert np.array_equal(got["s"], og.support())
+    for k in ks:
+        mask, sup, left = og.ktruss(k)
+        gm, gc = got["masks"][k]
+        assert np.array_equal(gm, mask), f"k={k}"
+        assert gc == left, f"k={k}"
+    kmax, truss = og.truss_decomposition()
+    assert got["kmax"] == kmax
+    assert np.array_equal(got["truss"], truss)
+    return got
+
+
+def test_fig1_and_fig2_examples():
+    fx = read_fixture("fig1_diamond.txt")
+    e = np.array(fx["edge"], dtype=np.int32)
+    got = check(e[:, 0], e[:, 1], 4)
+    assert got["T"] == fx["triangles"][0][0]
+    assert got["s"].tolist() == fx["support"][0]
+    fx = read_fixture("fig2_pendant.txt")
+    e = np.array(fx["edge"], dtype=np.int32)
+    got = check(e[:, 0], e[:, 1], 4)
+    assert got["masks"][3][0].tolist() == fx["truss3"][0]
+
+
+@pytest.mark.parametrize("n", [3, 4, 9, 33, 64])
+def test_complete_graphs(n):
+    s, d, _ = graphgen.complete(n)
+    got = check(s, d, n, ks=(2, 3, n, n + 1))
+    assert got["kmax"] == n
+
+
+@pytest.mark.parametrize("M", [2, 3, 16, 100])
+def test_image_graphs(M):
+    s, d, n = graphgen.king(M)
+    got = check(s, d, n)
+    assert got["T"] == 4 * (M - 1) ** 2 and got["kmax"] == 4
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: graphgen.star(5000), lambda: graphgen.path(3000),
+    lambda: graphgen.random_tree(4000, 1), lambda: graphgen.grid4(40)])
+def test_triangle_free(maker):
+    s, d, n = maker()
+    got = check(s, d, n)
+    assert got["T"] == 0 and got["kmax"] == 2
+
+
+def test_er4096_workload():
+    w = graphgen.WORKLOADS["er4096"]
+    s, d, n = w.generate()
+    check(s, d, n)
+
+
+@pytest.mark.parametrize("scale,seed", [(6, 1), (9, 2), (12, 3), (14, 4), (16, 5)])
+def test_rmat_graphs(scale, seed):
+    s, d, n = graphgen.rmat(scale, seed=seed)
+    check(s, d, n, ks=(3, 4, 6, 8))
+
+
+@pytest.mark.parametrize("m_in", [1, 2, 31, 33, 2047, 2049, 4095, 4096, 4097, 3 * 4096 + 5,
+                                  70001])
+def test_ragged_sizes(m_in):
+    rng = np.random.default_rng(m_in)
+    n = max(2, int(np.sqrt(m_in) * 3))
+    s = rng.integers(0, n, m_in).astype(np.int32)
+    d = rng.integers(0, n, m_in).astype(np.int32)
+    check(s, d, n)
+
+
+def test_messy_inputs_clean_to_the_same_graph():
+    s, d, n = graphgen.rmat(11, seed=7)
+    ms, md = graphgen.messy(s, d, seed=3, loops=500, dup_frac=0.3, flip_frac=0.4)
+    a = check(s, d, n)
+    b = check(ms, md, n)
+    assert np.array_equal(a["lo"], b["lo"]) and np.array_equal(a["s"], b["s"])
+
+
+def test_star_plus_clique_max_degree():
+    # hub adjacent to every vertex plus a dense core: maximum-degree vertex,
+    # skewed list lengths in every intersection
+    n = 20000
+    s = [np.zeros(n - 1, np.int32)]
+    d = [np.arange(1, n, dtype=np.int32)]
+    cs, cd, _ = graphgen.complete(40)
+    s.append(cs + 1)
+    d.append(cd + 1)
+    es, ed, _ = graphgen.er(n, 30000, seed=2)
+    s.append(es)
+    d.append(ed)
+    check(np.concatenate(s), np.concatenate(d), n, ks=(3, 4, 10, 41, 42))
+
+
+def test_degenerate_graphs():
+    # no edges at all
+    g = tc.tc_build_csr(dev(np.zeros(0)), dev(np.zeros(0)), 5)
+    assert g.m == 0 and tc.tc_count(g) == 0
+    s, T = tc.tc_edge_support(g)
+    assert T == 0 and s.numel() == 0
+    mask, left = tc.ktruss(g, 3)
+    assert left == 0
+    assert tc.ktruss_max(g)[0] == 0
+    g.free()
+    # only self-loops
+    g = tc.tc_build_csr(dev([0, 1, 2]), dev([0, 1, 2]), 3)
+    assert g.m == 0 and tc.ktruss_max(g)[0] == 0
+    g.free()
+    # one vertex
+    g = tc.tc_build_csr(dev([0]), dev([0]), 1)
+    assert g.m == 0 and tc.tc_count(g) == 0
+    g.free()
+    # single edge
+    got = check(np.array([1]), np.array([0]), 2)
+    assert got["kmax"] == 2 and got["truss"].tolist() == [2]
+
+
+def test_host_inputs_and_outputs():
+    s, d, n = graphgen.rmat(12, seed=11)
+    g = tc.tc_build_csr(s, d, n)            # numpy (host) inputs
+    og = oracle.OracleGraph.from_edges(s, d, n)
+    out = torch.empty(g.m, dtype=torch.int32)          # host output
+    sup, T = tc.tc_edge_support(g, out=out)
+    assert sup is out and np.array_equal(out.numpy(), og.support())
+    mask = torch.empty(g.m, dtype=torch.uint8)
+    tc.ktruss(g, 4, out=mask)
+    assert np.array_equal(mask.numpy(), og.ktruss(4)[0])
+    truss = torch.empty(g.m, dtype=torch.int32).pin_memory()
+    kmax, _ = tc.ktruss_max(g, out=truss)
+    assert kmax == og.truss_decomposition()[0]
+    assert np.array_equal(truss.numpy(), og.truss_decomposition()[1])
+    lo, hi = tc.tc_edges(g, device="cpu")
+    assert np.array_equal(lo.numpy(), og.lo)
+    g.free()
+
+
+def test_streams():
+    s, d, n = graphgen.rmat(13, seed=12)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        g = tc.tc_build_csr(dev(s), dev(d), n, stream=st)
+        T = tc.tc_count(g, stream=st)
+    assert T == oracle.OracleGraph.from_edges(s, d, n).count()
+    g.free()
+
+
+def test_errors_are_reported_and_leave_the_library_usable():
+    with pytest.raises(tc.TCError) as ei:
+        tc.tc_build_csr(dev([0, 1, 7]), dev([1, 2, 0]), 5)
+    assert ei.value.code == tc.TC_ERANGE
+    with pytest.raises(tc.TCError) as ei:
+        tc.tc_build_csr(dev([0]), dev([1]), 0)
+    assert ei.value.code == tc.TC_EINVAL
+    g = tc.tc_build_csr(dev([0, 1, 2]), dev([1, 2, 0]), 3)
+    with pytest.raises(tc.TCError) as ei:
+        tc.ktruss(g, 1)
+    assert ei.value.code == tc.TC_EINVAL
+    # host-side fault injection: the 3rd device allocation fails
+    tc.tc_debug_fail_alloc(3)
+    with pytest.raises(tc.TCError) as ei:
+        tc.tc_build_csr(dev([0, 1, 2]), dev([1, 2, 0]), 3)
+    assert ei.value.code == tc.TC_ENOMEM
+    tc.tc_debug_fail_alloc(0)
+    assert tc.tc_count(g) == 1
+    g.free()
+    g = tc.tc_build_csr(dev([0, 1, 2]), dev([1, 2, 0]), 3)
+    assert tc.ktruss_max(g)[0] == 3
+    g.free()
+
+
+# ------------------------------------------------- full-size R-MAT scale 20
+
+def _sha(a):
+    return hashlib.sha256(np.ascontiguousarray(a, dtype="<i4").tobytes()).hexdigest()
+
+
+def _fixture(name):
+    path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.txt")
+    if not os.path.exists(path):
+        pytest.skip(f"stored oracle results {path} not present")
+    out = {}
+    for line in open(path):
+        line = line.split("#", 1)[0].split()
+        if line:
+            out.setdefault(line[0], []).append(line[1:])
+    return out
+
+
+def test_rmat20_full_size_against_stored_oracle():
+    """R-MAT scale 20 in the bench's configuration: the whole path against the
+    oracle's stored results (hashes of every per-edge array)."""
+    fx = _fixture("rmat20")
+    w = graphgen.WORKLOADS["rmat20"]
+    s, d, n = w.generate()
+    g = tc.tc_build_csr(dev(s), dev(d), n)
+    assert g.m == int(fx["m"][0][0])
+    lo, hi = tc.tc_edges(g)
+    assert [_sha(lo.cpu().numpy()), _sha(hi.cpu().numpy())] == fx["lo_hi_sha256"][0]
+    T = tc.tc_count(g)
+    assert T == int(fx["triangles"][0][0])
+    sup, T2 = tc.tc_edge_support(g)
+    assert T2 == T
+    assert _sha(sup.cpu().numpy()) == fx["support_sha256"][0][0]
+    for k, left, h in fx.get("ktruss", []):
+        mask, c = tc.ktruss(g, int(k))
+        assert c == int(left)
+        assert _sha(mask.cpu().numpy().astype(np.int32)) == h
+    kmax, truss = tc.ktruss_max(g)
+    assert kmax == int(fx["kmax"][0][0])
+    assert _sha(truss.cpu().numpy()) == fx["truss_sha256"][0][0]
+    g.free()
