@@ -150,6 +150,10 @@ typedef struct {
     int64_t wedge_work;    /* sum over oriented edges (u, v) of |N+(u)| + |N+(v)|:
                               the list entries the masked product merges */
     int64_t device_bytes;  /* device memory held by the graph */
+    int64_t peel_rounds;   /* bulk removal rounds of the most recent ktruss /
+                              ktruss_max call on this graph (0 if none) */
+    int64_t peel_lists;    /* 1 if that call read precomputed per-edge triangle
+                              lists, 0 if it intersected neighbour lists */
 } tc_graph_info_t;
 
 /* Fills *info (host pointer).  Synchronises the stream. */
@@ -175,6 +179,24 @@ const char* tc_last_error(void);
  * out of memory; 0 disables.  Returns the previous setting.
  */
 int64_t tc_debug_fail_alloc(int64_t nth);
+
+/*
+ * Test hook: which form of the peel ktruss / ktruss_max use.  0 = automatic
+ * (per-edge triangle lists when they fit in free device memory, else
+ * intersections of live neighbour lists), 1 = always triangle lists (where
+ * the graph allows them), 2 = always intersections.  Both forms give the
+ * same results.  Returns the previous mode; other values leave it unchanged.
+ */
+int tc_debug_peel_mode(int mode);
+
+/*
+ * Test hook: which kernel tc_count / tc_edge_support use.  0 = automatic
+ * (one block per row with its out-list in a shared-memory hash table when
+ * the largest out-list fits, else one warp per oriented edge), 1 = the
+ * row kernel where the graph allows it, 2 = always one warp per edge.  Both
+ * give the same results.  Returns the previous mode.
+ */
+int tc_debug_intersect_mode(int mode);
 
 /*
  * Test hook: upper bound, in nanoseconds, on every device-side spin wait

@@ -28,9 +28,10 @@ from . import _build
 
 __all__ = [
     "TCError", "Graph", "load_library", "library_path", "tc_build_csr", "tc_count",
-    "tc_edge_support", "ktruss", "ktruss_max", "tc_num_edges", "tc_num_vertices", "tc_edges", "tc_graph_info", "tc_launch_count",
+    "tc_edge_support", "ktruss", "ktruss_max", "tc_num_edges", "tc_num_vertices", "tc_edges",
+    "tc_graph_info", "tc_launch_count",
     "tc_graph_free", "tc_strerror", "tc_last_error", "tc_debug_fail_alloc",
-    "tc_debug_spin_limit_ns", "TC_OK", "TC_EINVAL", "TC_ERANGE", "TC_ENOMEM", "TC_ECUDA",
+    "tc_debug_spin_limit_ns", "tc_debug_peel_mode", "tc_debug_intersect_mode", "TC_OK", "TC_EINVAL", "TC_ERANGE", "TC_ENOMEM", "TC_ECUDA",
     "TC_ETIMEDOUT", "TC_EOVERFLOW", "TC_INPUT_AUTO", "TC_INPUT_DEVICE", "TC_INPUT_HOST",
 ]
 
@@ -74,6 +75,8 @@ def load_library(build_if_missing: bool = True):
             "tc_launch_count": (i64, []),
             "tc_debug_fail_alloc": (i64, [i64]),
             "tc_debug_spin_limit_ns": (i64, [i64]),
+            "tc_debug_peel_mode": (ctypes.c_int, [ctypes.c_int]),
+            "tc_debug_intersect_mode": (ctypes.c_int, [ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -86,7 +89,8 @@ def load_library(build_if_missing: bool = True):
 class GraphInfo(ctypes.Structure):
     """Mirror of tc_graph_info_t."""
     _fields_ = [(f, ctypes.c_int64) for f in
-                ("n", "m_in", "m", "max_degree", "max_out", "wedge_work", "device_bytes")]
+                ("n", "m_in", "m", "max_degree", "max_out", "wedge_work", "device_bytes",
+                 "peel_rounds", "peel_lists")]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -289,6 +293,16 @@ def tc_graph_free(g: Graph):
 
 def tc_debug_fail_alloc(nth: int) -> int:
     return int(load_library().tc_debug_fail_alloc(int(nth)))
+
+
+def tc_debug_peel_mode(mode: int) -> int:
+    """0 automatic, 1 triangle lists, 2 intersections; returns the previous mode."""
+    return int(load_library().tc_debug_peel_mode(int(mode)))
+
+
+def tc_debug_intersect_mode(mode: int) -> int:
+    """0 automatic, 1 row/hash kernel, 2 edge-per-warp kernel; returns the previous mode."""
+    return int(load_library().tc_debug_intersect_mode(int(mode)))
 
 
 def tc_debug_spin_limit_ns(ns: int) -> int:

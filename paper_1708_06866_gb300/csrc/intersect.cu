@@ -6,20 +6,146 @@
 // For an oriented edge (u, v), (L L^T)(u, v) = |N+(u) ∩ N+(v)|: each common
 // out-neighbour w closes the triangle u < v < w (in rank order), found only
 // at its lowest edge (u, v).  The support pass credits all three edges of
-// each triangle found: (u, v) by the count, (u, w) and (v, w) by atomics.
+// each triangle found: (u, v) and (v, w) by global atomics, (u, w) through a
+// per-row shared-memory counter flushed once per row.
+//
+// Main kernel (k_rows): one block per row u, rows handed out dynamically from
+// the highest rank down.  N+(u) goes into a shared-memory hash table (key =
+// neighbour, value = its position in the row); each warp takes one v of
+// N+(u) at a time and its lanes stream N+(v) with coalesced loads, probing
+// the table for every w.  A third mode writes each edge's triangle list (the
+// ids of the two other edges of every triangle through it) for the peel.
+// Graphs whose largest out-list exceeds the table capacity use k_edges_warp
+// (one warp per oriented edge, binary search in global memory).
 #include <algorithm>
+#include <climits>
 
 #include "tc_internal.cuh"
 
 namespace tc {
 namespace {
 
+constexpr int RX_THREADS = 256;
+constexpr int RX_WARPS = RX_THREADS / 32;
+constexpr int RX_MAX_OUT = 8192;  // largest |N+(u)| the shared table holds (load <= 1/2)
 constexpr int IX_THREADS = 256;
 
-// One warp per oriented edge: lanes take the shorter out-list's elements and
-// look each up in the longer list by binary search.
+enum Mode { COUNT = 0, SUPPORT = 1, LISTS = 2 };
+
+__device__ __forceinline__ uint32_t slot_of(int32_t w, int log_cap) {
+    return ((uint32_t)w * 0x9E3779B1u) >> (32 - log_cap);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(RX_THREADS) k_rows(
+    const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
+    const int32_t* __restrict__ col, const int32_t* __restrict__ eid, int32_t n,
+    int32_t* __restrict__ sup, unsigned int* __restrict__ cursor,
+    int2* __restrict__ pairs, unsigned int* __restrict__ next_row,
+    unsigned long long* __restrict__ partials, int max_log_cap) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int max_cap = 1 << max_log_cap;
+    int32_t* keys = reinterpret_cast<int32_t*>(smem);
+    uint16_t* pos = reinterpret_cast<uint16_t*>(keys + max_cap);
+    int32_t* cnt = reinterpret_cast<int32_t*>(pos + max_cap);  // SUPPORT: per position of N+(u)
+    __shared__ int s_row;
+    __shared__ unsigned long long s_acc[RX_WARPS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long acc = 0;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_row = (int)atomicAdd(next_row, 1u);
+        __syncthreads();
+        const int r = s_row;
+        __syncthreads();
+        if (r >= n) break;
+        const int32_t u = n - 1 - r;
+        const int64_t a0 = upper[u];
+        const int du = (int)(rowptr[u + 1] - a0);
+        if (du < 2) continue;
+        int log_cap = 6;
+        while ((1 << log_cap) < 2 * du) ++log_cap;
+        const int cap = 1 << log_cap;
+        for (int i = threadIdx.x; i < cap; i += RX_THREADS) keys[i] = -1;
+        if (MODE == SUPPORT)
+            for (int i = threadIdx.x; i < du; i += RX_THREADS) cnt[i] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < du; i += RX_THREADS) {
+            const int32_t w = col[a0 + i];
+            uint32_t h = slot_of(w, log_cap);
+            while (atomicCAS(&keys[h], -1, w) != -1) h = (h + 1) & (cap - 1);
+            pos[h] = (uint16_t)i;
+        }
+        __syncthreads();
+        const int32_t umax = col[a0 + du - 1];
+        // the largest v of N+(u) cannot close a triangle: nothing in N+(u) is above it
+        for (int j = warp; j < du - 1; j += RX_WARPS) {
+            const int32_t v = col[a0 + j];
+            const int64_t b0 = upper[v], b1 = rowptr[v + 1];
+            const int32_t e_uv = MODE == COUNT ? 0 : eid[a0 + j];
+            uint32_t c = 0;
+            for (int64_t cb = b0; cb < b1; cb += 32) {
+                const int64_t p = cb + lane;
+                const int32_t w = p < b1 ? col[p] : INT_MAX;
+                // rows ascend: once a chunk starts above max N+(u), nothing later matches
+                if (__shfl_sync(0xffffffffu, w, 0) > umax) break;
+                bool hit = false;
+                uint32_t h = 0;
+                if (w <= umax) {
+                    h = slot_of(w, log_cap);
+                    int32_t kk;
+                    while ((kk = keys[h]) != -1 && kk != w) h = (h + 1) & (cap - 1);
+                    hit = kk == w;
+                }
+                if (MODE == LISTS) {
+                    // the triangles of this chunk share edge (u, v): one append for all
+                    const unsigned msk = __ballot_sync(0xffffffffu, hit);
+                    if (msk) {
+                        const int ldr = __ffs(msk) - 1;
+                        unsigned base = 0;
+                        if (lane == ldr) base = atomicAdd(&cursor[e_uv], (unsigned)__popc(msk));
+                        base = __shfl_sync(0xffffffffu, base, ldr);
+                        if (hit) {
+                            const int32_t e_uw = eid[a0 + pos[h]], e_vw = eid[p];
+                            pairs[base + __popc(msk & lanemask_lt())] = make_int2(e_uw, e_vw);
+                            pairs[atomicAdd(&cursor[e_uw], 1u)] = make_int2(e_uv, e_vw);
+                            pairs[atomicAdd(&cursor[e_vw], 1u)] = make_int2(e_uv, e_uw);
+                        }
+                    }
+                }
+                if (hit) {
+                    ++c;
+                    if (MODE == SUPPORT) {
+                        atomicAdd(&cnt[pos[h]], 1);
+                        atomicAdd(&sup[eid[p]], 1);
+                    }
+                }
+            }
+            c = warp_sum(c);
+            if (lane == 0) {
+                acc += c;
+                if (MODE == SUPPORT && c) atomicAdd(&sup[e_uv], (int)c);
+            }
+        }
+        __syncthreads();
+        if (MODE == SUPPORT)
+            for (int i = threadIdx.x; i < du; i += RX_THREADS)
+                if (cnt[i]) atomicAdd(&sup[eid[a0 + i]], cnt[i]);
+        __syncthreads();
+    }
+    if (lane == 0) s_acc[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < RX_WARPS; ++w) t += s_acc[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+// Fallback: one warp per oriented edge; lanes take the shorter out-list's
+// elements and look each up in the longer list by binary search.
 template <bool SUPPORT>
-__global__ void __launch_bounds__(IX_THREADS) k_intersect_warp(
+__global__ void __launch_bounds__(IX_THREADS) k_edges_warp(
     const int32_t* __restrict__ fwd, const int2* __restrict__ ends,
     const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
     const int32_t* __restrict__ col, const int32_t* __restrict__ eid, int64_t m,
@@ -34,7 +160,7 @@ __global__ void __launch_bounds__(IX_THREADS) k_intersect_warp(
         int64_t s0 = upper[uv.x], s1 = rowptr[uv.x + 1];
         int64_t l0 = upper[uv.y], l1 = rowptr[uv.y + 1];
         if (s1 - s0 > l1 - l0) {
-            int64_t t0 = s0, t1 = s1;
+            const int64_t t0 = s0, t1 = s1;
             s0 = l0;
             s1 = l1;
             l0 = t0;
@@ -105,6 +231,147 @@ __global__ void k_wedge_work(const int32_t* __restrict__ fwd, const int2* __rest
     if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
 
+// ---- 64-bit exclusive scan of int32 values (offsets of the triangle lists)
+
+constexpr int SC_THREADS = 256;
+constexpr int SC_ITEMS = 8;
+constexpr int SC_CHUNK = SC_THREADS * SC_ITEMS;
+
+__device__ unsigned long long block_sum64(unsigned long long v, unsigned long long* sh) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned long long t = 0;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        sh[32] = t;
+    }
+    __syncthreads();
+    t = sh[32];
+    __syncthreads();
+    return t;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_chunk_sums(const int32_t* __restrict__ x,
+                                                           int64_t n,
+                                                           unsigned long long* __restrict__ sums) {
+    __shared__ unsigned long long sh[33];
+    const int64_t base = (int64_t)blockIdx.x * SC_CHUNK;
+    unsigned long long v = 0;
+    for (int i = threadIdx.x; i < SC_CHUNK; i += SC_THREADS)
+        if (base + i < n) v += (unsigned long long)x[base + i];
+    const unsigned long long t = block_sum64(v, sh);
+    if (threadIdx.x == 0) sums[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_sums64(unsigned long long* __restrict__ v,
+                                                      int64_t count) {
+    __shared__ unsigned long long sh[1024];
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < count; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const unsigned long long x = i < count ? v[i] : 0ull;
+        sh[threadIdx.x] = x;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan
+            const unsigned long long y = threadIdx.x >= o ? sh[threadIdx.x - o] : 0ull;
+            __syncthreads();
+            sh[threadIdx.x] += y;
+            __syncthreads();
+        }
+        if (i < count) v[i] = carry + sh[threadIdx.x] - x;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += sh[1023];
+        __syncthreads();
+    }
+}
+
+// off[i] = sum of x[0..i); off[n] = total.
+__global__ void __launch_bounds__(SC_THREADS) k_chunk_scan(const int32_t* __restrict__ x, int64_t n,
+                                                           const unsigned long long* __restrict__ sums,
+                                                           unsigned long long* __restrict__ off) {
+    __shared__ unsigned long long sh[SC_THREADS];
+    const int64_t base = (int64_t)blockIdx.x * SC_CHUNK;
+    // each thread owns SC_ITEMS consecutive values
+    unsigned long long loc[SC_ITEMS];
+    unsigned long long tsum = 0;
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k) {
+        const int64_t i = base + (int64_t)threadIdx.x * SC_ITEMS + k;
+        loc[k] = i < n ? (unsigned long long)x[i] : 0ull;
+        tsum += loc[k];
+    }
+    sh[threadIdx.x] = tsum;
+    __syncthreads();
+    for (int o = 1; o < SC_THREADS; o <<= 1) {
+        const unsigned long long y = threadIdx.x >= o ? sh[threadIdx.x - o] : 0ull;
+        __syncthreads();
+        sh[threadIdx.x] += y;
+        __syncthreads();
+    }
+    unsigned long long run = sums[blockIdx.x] + sh[threadIdx.x] - tsum;
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k) {
+        const int64_t i = base + (int64_t)threadIdx.x * SC_ITEMS + k;
+        if (i < n) off[i] = run;
+        if (i == n - 1) off[n] = run + loc[k];
+        run += loc[k];
+    }
+}
+
+__global__ void k_u32_from_u64(const unsigned long long* __restrict__ in, int64_t n,
+                               unsigned int* __restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = (unsigned int)in[i];
+}
+
+int rows_log_cap(const Graph* g) {
+    int lc = 6;
+    while ((1 << lc) < 2 * g->max_out) ++lc;
+    return lc;
+}
+
+size_t rows_smem(int log_cap, int mode) {
+    const size_t cap = (size_t)1 << log_cap;
+    return cap * 4 + cap * 2 + (mode == SUPPORT ? (cap / 2) * 4 : 0) + 16;
+}
+
+template <int MODE>
+int launch_rows(Graph* g, int32_t* sup, unsigned int* cursor, int2* pairs,
+                unsigned long long* partials, int blocks, cudaStream_t s) {
+    const int lc = rows_log_cap(g);
+    const size_t sm = rows_smem(lc, MODE);
+    TC_CUDA_TRY(cudaFuncSetAttribute(k_rows<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sm));
+    unsigned int* next_row = reinterpret_cast<unsigned int*>(g->dev_scalars + 4);
+    TC_CUDA_TRY(cudaMemsetAsync(next_row, 0, sizeof(unsigned int), s));
+    k_rows<MODE><<<blocks, RX_THREADS, sm, s>>>(g->rowptr, g->upper, g->col, g->eid, g->n, sup,
+                                                cursor, pairs, next_row, partials, lc);
+    TC_LAUNCH_CHECK("k_rows");
+    return TC_OK;
+}
+
+int rows_blocks(Graph* g, int mode) {
+    int per_sm = 0;
+    const size_t sm = rows_smem(rows_log_cap(g), mode);
+    cudaError_t e = cudaSuccess;
+    if (mode == COUNT) {
+        cudaFuncSetAttribute(k_rows<COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows<COUNT>, RX_THREADS, sm);
+    } else if (mode == SUPPORT) {
+        cudaFuncSetAttribute(k_rows<SUPPORT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows<SUPPORT>, RX_THREADS, sm);
+    } else {
+        cudaFuncSetAttribute(k_rows<LISTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows<LISTS>, RX_THREADS, sm);
+    }
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    return num_sms() * per_sm;
+}
+
 }  // namespace
 
 int graph_wedge_work(Graph* g, int64_t* out, cudaStream_t s) {
@@ -131,19 +398,25 @@ int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangle
         if (triangles) *triangles = 0;
         return TC_OK;
     }
-    const int blocks = num_sms() * 8;
+    const bool rows = g->max_out <= RX_MAX_OUT && intersect_mode() != 2;
+    const int blocks = rows ? rows_blocks(g, want_support ? SUPPORT : COUNT) : num_sms() * 8;
     Scratch sc(s);
     unsigned long long* partials;
     TC_TRY(sc.alloc(&partials, blocks));
-    if (want_support) {
-        TC_CUDA_TRY(cudaMemsetAsync(sup, 0, sizeof(int32_t) * m, s));
-        k_intersect_warp<true><<<blocks, IX_THREADS, 0, s>>>(g->fwd, g->ends, g->rowptr, g->upper,
-                                                             g->col, g->eid, m, sup, partials);
+    if (want_support) TC_CUDA_TRY(cudaMemsetAsync(sup, 0, sizeof(int32_t) * m, s));
+    if (rows) {
+        if (want_support)
+            TC_TRY(launch_rows<SUPPORT>(g, sup, nullptr, nullptr, partials, blocks, s));
+        else TC_TRY(launch_rows<COUNT>(g, nullptr, nullptr, nullptr, partials, blocks, s));
+    } else if (want_support) {
+        k_edges_warp<true><<<blocks, IX_THREADS, 0, s>>>(g->fwd, g->ends, g->rowptr, g->upper,
+                                                         g->col, g->eid, m, sup, partials);
+        TC_LAUNCH_CHECK("k_edges_warp");
     } else {
-        k_intersect_warp<false><<<blocks, IX_THREADS, 0, s>>>(g->fwd, g->ends, g->rowptr, g->upper,
-                                                              g->col, g->eid, m, nullptr, partials);
+        k_edges_warp<false><<<blocks, IX_THREADS, 0, s>>>(g->fwd, g->ends, g->rowptr, g->upper,
+                                                          g->col, g->eid, m, nullptr, partials);
+        TC_LAUNCH_CHECK("k_edges_warp");
     }
-    TC_LAUNCH_CHECK("k_intersect_warp");
     k_reduce_partials<<<1, 1024, 0, s>>>(partials, blocks, g->dev_scalars);
     TC_LAUNCH_CHECK("k_reduce_partials");
     if (triangles) {
@@ -152,6 +425,41 @@ int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangle
         TC_CUDA_TRY(cudaStreamSynchronize(s));
         *triangles = (int64_t)t;
     }
+    return TC_OK;
+}
+
+bool triangle_lists_supported(const Graph* g) { return g->max_out <= RX_MAX_OUT; }
+
+int exclusive_scan_i32(const int32_t* x, int64_t n, unsigned long long* off, cudaStream_t s) {
+    const int64_t chunks = (n + SC_CHUNK - 1) / SC_CHUNK;
+    Scratch sc(s);
+    unsigned long long* sums;
+    TC_TRY(sc.alloc(&sums, chunks));
+    k_chunk_sums<<<(unsigned)chunks, SC_THREADS, 0, s>>>(x, n, sums);
+    TC_LAUNCH_CHECK("k_chunk_sums");
+    k_scan_sums64<<<1, 1024, 0, s>>>(sums, chunks);
+    TC_LAUNCH_CHECK("k_scan_sums64");
+    k_chunk_scan<<<(unsigned)chunks, SC_THREADS, 0, s>>>(x, n, sums, off);
+    TC_LAUNCH_CHECK("k_chunk_scan");
+    return TC_OK;
+}
+
+int build_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off, int2* pairs,
+                         cudaStream_t s) {
+    const int64_t m = g->m;
+    TC_TRY(exclusive_scan_i32(sup, m, off, s));
+    Scratch sc(s);
+    // list positions fit in 32 bits (the caller keeps 3T below 2^32): a
+    // 4-byte cursor per edge keeps the cursor array small enough for L2
+    unsigned int* cursor;
+    TC_TRY(sc.alloc(&cursor, m));
+    k_u32_from_u64<<<(unsigned)std::min<int64_t>((m + 255) / 256, (int64_t)num_sms() * 16), 256, 0,
+                     s>>>(off, m, cursor);
+    TC_LAUNCH_CHECK("k_u32_from_u64");
+    const int blocks = rows_blocks(g, LISTS);
+    unsigned long long* partials;
+    TC_TRY(sc.alloc(&partials, blocks));
+    TC_TRY(launch_rows<LISTS>(g, nullptr, cursor, pairs, partials, blocks, s));
     return TC_OK;
 }
 

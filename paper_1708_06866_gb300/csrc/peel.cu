@@ -11,119 +11,422 @@
 //   triangle with the smallest edge id, which lowers s of each of f, g that
 //   is not dying.  An edge whose support falls from k - 2 to k - 3 (exactly
 //   one atomic sees that) joins the next round's frontier;
-//   then the dying edges are removed (state = truss number k - 1).
+//   then the dying edges are removed (state = k - 1, their truss number).
 // The decomposition runs k = 3, 4, ... on the survivors of the previous level
 // until no edge is left.
 //
+// All levels and rounds run inside one persistent cooperative kernel whose
+// blocks meet at grid barriers between phases; every barrier wait is bounded
+// in time (on expiry the kernel sets an abort flag and every block returns).
+// When at least half of the adjacency entries belong to removed edges, the
+// rows are compacted in place so later rounds scan only live entries.
+//
 // Edge state t[e]: 0 = alive, -1 = in the current frontier, > 0 = removed.
 #include <algorithm>
-#include <utility>
+#include <climits>
 
 #include "tc_internal.cuh"
 
 namespace tc {
 namespace {
 
-constexpr int PL_THREADS = 256;
+constexpr int PK_THREADS = 512;
+constexpr int PK_WARPS = PK_THREADS / 32;
+constexpr int WINDOW = 8;        // support values one full scan covers (see k_peel)
+constexpr int64_t HEAVY = 4096;  // triangle-list length above which an edge is "heavy"
+
+struct PeelCtl {
+    unsigned long long bar;      // grid-barrier arrivals (monotonic)
+    unsigned long long cntA[2];  // alive-list appends, by full-scan parity (monotonic)
+    unsigned long long cntW[2];  // window-list appends, by level parity
+    unsigned long long cntF[2];  // light-frontier appends, by round parity
+    unsigned long long cntH[2];  // heavy-frontier appends, by round parity
+    int abort;                   // 1 = a barrier wait ran out of time
+    int kmax;                    // decomposition result
+    int overflow;                // 1 = the round table ran out (not expected)
+    int pad;
+    long long n_alive;           // edges left after the last level
+    long long rounds;            // non-empty rounds
+    long long compactions;
+    long long full_scans;
+};
+
+struct PeelArgs {
+    int64_t m;
+    int32_t n;
+    const int2* ends;
+    const int64_t* rowptr;
+    int32_t* rowlen;  // live length of each row (rows compact in place)
+    int32_t* col;     // working copies of the adjacency
+    int32_t* eid;
+    int32_t* t;       // edge state (see below)
+    int32_t* s;
+    int32_t* A[2];    // alive lists
+    int32_t* W[2];    // window lists
+    int32_t* F[2];    // light frontiers
+    int32_t* H[2];    // heavy frontiers
+    int32_t* level_of;  // level k of each round number
+    int64_t max_round;  // entries of level_of
+    PeelCtl* ctl;
+    const unsigned long long* off;  // triangle-list mode: list of edge e = pairs[off[e]..off[e+1])
+    const int2* pairs;              // the two other edges of each triangle through e
+    int32_t k_first;
+    int32_t single;  // 1: peel level k_first only
+    int64_t spin_ns;
+};
+
+// Loads of data that other blocks write during the kernel go through L2.
+__device__ __forceinline__ int ld_cg(const int32_t* p) { return __ldcg(p); }
+
+__device__ __forceinline__ unsigned long long ld_vol(const unsigned long long* p) {
+    return *(const volatile unsigned long long*)p;
+}
+
+// Grid barrier: monotonic arrival counter; bounded wait.  Returns false on
+// abort (every caller then returns from the kernel).
+__device__ bool grid_sync(PeelCtl* ctl, unsigned long long* epoch, int64_t spin_ns, int* s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        *epoch += 1;
+        const unsigned long long target = *epoch * (unsigned long long)gridDim.x;
+        __threadfence();
+        atomicAdd(&ctl->bar, 1ull);
+        uint64_t t0 = 0;
+        while (ld_acquire_u64(reinterpret_cast<const uint64_t*>(&ctl->bar)) < target) {
+            if (*(volatile int*)&ctl->abort) {
+                ok = 0;
+                break;
+            }
+            const uint64_t now = global_timer_ns();
+            if (t0 == 0) {
+                t0 = now;
+            } else if ((int64_t)(now - t0) > spin_ns) {
+                atomicExch(&ctl->abort, 1);
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
 
 __device__ __forceinline__ void warp_append(bool take, int32_t value, int32_t* list,
-                                            unsigned* count) {
+                                            unsigned long long* counter,
+                                            unsigned long long base) {
     const unsigned mask = __ballot_sync(0xffffffffu, take);
     if (mask == 0) return;
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(mask) - 1;
-    unsigned base = 0;
-    if (lane == leader) base = atomicAdd(count, (unsigned)__popc(mask));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (take) list[base + __popc(mask & lanemask_lt())] = value;
+    unsigned long long pos = 0;
+    if (lane == leader) pos = atomicAdd(counter, (unsigned long long)__popc(mask));
+    pos = __shfl_sync(0xffffffffu, pos, leader);
+    if (take) list[pos - base + __popc(mask & lanemask_lt())] = value;
 }
 
-// Level start: keep the edges of `in` that are still alive (-> out) and put
-// those with s < thr into the frontier, marked dying.  in == NULL means all
-// edges 0..n_in-1.
-__global__ void __launch_bounds__(PL_THREADS) k_level_scan(
-    const int32_t* __restrict__ in, int64_t n_in, int32_t* __restrict__ t,
-    const int32_t* __restrict__ s, int32_t thr, int32_t* __restrict__ out,
-    unsigned* __restrict__ n_out, int32_t* __restrict__ F, unsigned* __restrict__ nF) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t start = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (int64_t base = start - (threadIdx.x & 31); base < n_in; base += stride) {
-        const int64_t i = base + (threadIdx.x & 31);
-        bool alive = false, front = false;
-        int32_t e = 0;
-        if (i < n_in) {
-            e = in ? in[i] : (int32_t)i;
-            alive = t[e] == 0;
-            front = alive && s[e] < thr;
-            if (front) t[e] = -1;
+// Edge states during round r: 0 = alive; -r = in round r's frontier (dying);
+// -(r + 1) = alive, already in the next frontier; -q with q < r = removed in
+// round q.  Stamping states with round numbers needs no pass that retires a
+// frontier: the next round reads the round number instead.
+struct Round {
+    int32_t r;
+    __device__ bool removed(int32_t st) const { return st < 0 && st > -r; }
+    __device__ bool dying(int32_t st) const { return st == -r; }
+    __device__ bool alive(int32_t st) const { return st == 0 || st == -(r + 1); }
+};
+
+// Where a round's appends go (counters and bases are uniform per phase).
+struct Sinks {
+    int32_t* Fn;
+    int32_t* Hn;
+    int32_t* Wc;
+    unsigned long long* cntF;
+    unsigned long long* cntH;
+    unsigned long long* cntW;
+    unsigned long long baseF, baseH, baseW;
+    int32_t thr;    // frontier threshold k - 2
+    int32_t bound;  // window bound: the window list holds alive edges with s < bound
+};
+
+template <bool TL>
+__device__ __forceinline__ bool is_heavy(const PeelArgs& a, int32_t e) {
+    return TL && (int64_t)(a.off[e + 1] - a.off[e]) > HEAVY;
+}
+
+// Lowers the support of alive edge x by one; x joins the next frontier when
+// its support falls from k - 2 to k - 3 and the window list when it falls to
+// just below the window bound (exactly one atomic sees each crossing).
+template <bool TL>
+__device__ __forceinline__ void lower(const PeelArgs& a, Round rd, int32_t x, const Sinks& k) {
+    const int old = atomicSub(a.s + x, 1);
+    if (old == k.thr) {
+        a.t[x] = -(rd.r + 1);
+        if (is_heavy<TL>(a, x)) k.Hn[atomicAdd(k.cntH, 1ull) - k.baseH] = x;
+        else k.Fn[atomicAdd(k.cntF, 1ull) - k.baseF] = x;
+    }
+    if (old == k.bound) k.Wc[atomicAdd(k.cntW, 1ull) - k.baseW] = x;
+}
+
+// A frontier edge's triangle {e, f, g} whose other two edges are not yet
+// removed is destroyed this round; the smallest dying edge of the triangle
+// owns it and lowers the support of each of f, g that is not dying.
+template <bool TL>
+__device__ __forceinline__ void destroy(const PeelArgs& a, Round rd, int32_t e, int32_t f,
+                                        int32_t tf, int32_t g, int32_t tg, const Sinks& k) {
+    if ((rd.dying(tf) && f < e) || (rd.dying(tg) && g < e)) return;
+    if (rd.alive(tf)) lower<TL>(a, rd, f, k);
+    if (rd.alive(tg)) lower<TL>(a, rd, g, k);
+}
+
+// All triangles through frontier edge e, by a group of gsize lanes.
+template <bool TL>
+__device__ __forceinline__ void process_edge(const PeelArgs& a, Round rd, int32_t e,
+                                             int64_t glane, int64_t gsize, const Sinks& k) {
+    if (TL) {
+        const int64_t q0 = (int64_t)a.off[e], q1 = (int64_t)a.off[e + 1];
+        for (int64_t q = q0 + glane; q < q1; q += gsize) {
+            const int2 fg = a.pairs[q];
+            const int32_t tf = ld_cg(a.t + fg.x);
+            if (rd.removed(tf)) continue;
+            const int32_t tg = ld_cg(a.t + fg.y);
+            if (rd.removed(tg)) continue;
+            destroy<TL>(a, rd, e, fg.x, tf, fg.y, tg, k);
         }
-        warp_append(alive, e, out, n_out);
-        warp_append(front, e, F, nF);
+        return;
+    }
+    const int2 ab = a.ends[e];
+    int64_t s0 = a.rowptr[ab.x], l0 = a.rowptr[ab.y];
+    int32_t sl = ld_cg(a.rowlen + ab.x), ll = ld_cg(a.rowlen + ab.y);
+    if (sl > ll) {
+        const int64_t t0 = s0;
+        s0 = l0;
+        l0 = t0;
+        const int32_t t1 = sl;
+        sl = ll;
+        ll = t1;
+    }
+    for (int64_t p = glane; p < sl; p += gsize) {
+        const int32_t f = ld_cg(a.eid + s0 + p);
+        const int32_t tf = ld_cg(a.t + f);
+        if (rd.removed(tf)) continue;
+        const int32_t w = ld_cg(a.col + s0 + p);
+        int32_t lo = 0, hi = ll;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (ld_cg(a.col + l0 + mid) < w) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo >= ll || ld_cg(a.col + l0 + lo) != w) continue;
+        const int32_t g = ld_cg(a.eid + l0 + lo);
+        const int32_t tg = ld_cg(a.t + g);
+        if (rd.removed(tg)) continue;
+        destroy<TL>(a, rd, e, f, tf, g, tg, k);
     }
 }
 
-// One round: one warp per frontier edge e = {a, b}; lanes take the shorter
-// full neighbour list's entries and look each up in the longer list.
-__global__ void __launch_bounds__(PL_THREADS) k_peel_round(
-    const int32_t* __restrict__ F, unsigned nF, const int2* __restrict__ ends,
-    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-    const int32_t* __restrict__ eid, const int32_t* __restrict__ t, int32_t* __restrict__ s,
-    int32_t thr, int32_t* __restrict__ Fn, unsigned* __restrict__ nFn) {
+// Groups of W warps per edge (W a power of two, as wide as the list count
+// allows, spanning blocks when the list is short); each group takes edges
+// round-robin.
+template <bool TL>
+__device__ __forceinline__ void process_list(const PeelArgs& a, Round rd, const int32_t* L,
+                                             int64_t nL, int64_t gwarp, int64_t nwarps,
+                                             const Sinks& k) {
+    if (nL == 0) return;
+    int64_t W = 1;
+    while (nL * (W * 2) <= nwarps) W *= 2;
+    const int64_t ngroups = nwarps / W;
+    const int64_t group = gwarp / W;
+    if (group >= ngroups) return;
+    const int64_t glane = (gwarp % W) * 32 + (threadIdx.x & 31);
+    for (int64_t j = group; j < nL; j += ngroups)
+        process_edge<TL>(a, rd, ld_cg(L + j), glane, 32 * W, k);
+}
+
+// The peel.  Levels k = k_first, k_first + 1, ...; each level starts with a
+// scan that collects the edges below the threshold (the first frontier) and
+// then runs rounds until no frontier is left.  A full scan (of every alive
+// edge) also collects the "window": alive edges with support below
+// thr + WINDOW.  The next levels scan only the window, because every edge
+// that can join their frontiers is in it: supports only fall, and an edge
+// whose support falls below the window bound during a round is appended to
+// the window at that moment.  Once the threshold passes the bound, the next
+// level makes a full scan again.
+//
+// TL = true: each edge's triangles come from its precomputed triangle list;
+// TL = false: from the intersection of its endpoints' live neighbour lists.
+template <bool TL>
+__global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
+    __shared__ int s_ok;
+    unsigned long long epoch = 0;
+    PeelCtl* ctl = a.ctl;
     const int lane = threadIdx.x & 31;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t j = wid; j < (int64_t)nF; j += nw) {
-        const int32_t e = F[j];
-        const int2 ab = ends[e];
-        int64_t s0 = rowptr[ab.x], s1 = rowptr[ab.x + 1];
-        int64_t l0 = rowptr[ab.y], l1 = rowptr[ab.y + 1];
-        if (s1 - s0 > l1 - l0) {
-            const int64_t t0 = s0, t1 = s1;
-            s0 = l0;
-            s1 = l1;
-            l0 = t0;
-            l1 = t1;
+    const int wib = threadIdx.x >> 5;
+    const int64_t gwarp = (int64_t)blockIdx.x * PK_WARPS + wib;
+    const int64_t nwarps = (int64_t)gridDim.x * PK_WARPS;
+    const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+
+    unsigned long long baseA[2] = {0, 0}, baseW[2] = {0, 0}, baseF[2] = {0, 0},
+                       baseH[2] = {0, 0};
+    int ai = 0, wi = 0, fi = 0;  // which buffer of each pair is the current one
+    bool first = true;           // the first full scan reads every edge id
+    int64_t nA = a.m;            // entries of the current alive list
+    int64_t nW = 0;              // entries of the current window list
+    int64_t n_alive = a.m;
+    int64_t nnz = 2 * a.m;
+    int64_t rounds = 0, compactions = 0, fulls = 0;
+    int32_t k = a.k_first;
+    int32_t kmax = 2;
+    int32_t r = 1;  // round whose frontier the next level scan collects
+    int32_t bound = INT_MIN;
+    int level = 0;
+
+    for (;;) {
+        if (r + 2 >= a.max_round) {  // uniform: every block sees the same r
+            if (leader) ctl->overflow = 1;
+            return;
         }
-        for (int64_t p = s0 + lane; p < s1; p += 32) {
-            const int32_t f = eid[p];
-            const int32_t tf = t[f];
-            if (tf > 0) continue;  // removed in an earlier round
-            const int32_t w = col[p];
-            int64_t lo = l0, hi = l1;
-            while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if (col[mid] < w) lo = mid + 1;
-                else hi = mid;
-            }
-            if (lo >= l1 || col[lo] != w) continue;
-            const int32_t g = eid[lo];
-            const int32_t tg = t[g];
-            if (tg > 0) continue;
-            // the triangle is destroyed this round; its smallest dying edge owns it
-            if ((tf < 0 && f < e) || (tg < 0 && g < e)) continue;
-            if (tf == 0) {
-                const int old = atomicSub(&s[f], 1);
-                if (old == thr) Fn[atomicAdd(nFn, 1u)] = f;
-            }
-            if (tg == 0) {
-                const int old = atomicSub(&s[g], 1);
-                if (old == thr) Fn[atomicAdd(nFn, 1u)] = g;
+        const int32_t thr = k - 2;
+        const bool full = thr > bound;
+        if (full) bound = thr + WINDOW;
+        const int wp = level & 1, pf = r & 1, pa = (int)(fulls & 1);
+        if (leader) a.level_of[r] = k;
+        int32_t* Wout = a.W[wi ^ 1];
+        {
+            const int32_t* in = full ? (first ? nullptr : a.A[ai]) : a.W[wi];
+            const int64_t n_in = full ? nA : nW;
+            int32_t* Aout = a.A[ai ^ 1];
+            for (int64_t base = gwarp * 32; base < n_in; base += nwarps * 32) {
+                const int64_t i = base + lane;
+                bool alive = false, win = false, light = false, heavy = false;
+                int32_t e = 0;
+                if (i < n_in) {
+                    e = in ? ld_cg(in + i) : (int32_t)i;
+                    alive = ld_cg(a.t + e) == 0;
+                    if (alive) {
+                        const int32_t se = ld_cg(a.s + e);
+                        win = se < bound;
+                        if (se < thr) {
+                            a.t[e] = -r;
+                            heavy = is_heavy<TL>(a, e);
+                            light = !heavy;
+                        }
+                    }
+                }
+                if (full) warp_append(alive, e, Aout, &ctl->cntA[pa], baseA[pa]);
+                warp_append(win, e, Wout, &ctl->cntW[wp], baseW[wp]);
+                warp_append(light, e, a.F[fi], &ctl->cntF[pf], baseF[pf]);
+                warp_append(heavy, e, a.H[fi], &ctl->cntH[pf], baseH[pf]);
             }
         }
+        if (!grid_sync(ctl, &epoch, a.spin_ns, &s_ok)) return;
+        if (full) {
+            const unsigned long long endA = ld_vol(&ctl->cntA[pa]);
+            nA = (int64_t)(endA - baseA[pa]);
+            baseA[pa] = endA;
+            n_alive = nA;
+            ai ^= 1;
+            first = false;
+            ++fulls;
+        }
+        int64_t nF, nH;
+        {
+            const unsigned long long eF = ld_vol(&ctl->cntF[pf]), eH = ld_vol(&ctl->cntH[pf]);
+            nF = (int64_t)(eF - baseF[pf]);
+            nH = (int64_t)(eH - baseH[pf]);
+            baseF[pf] = eF;
+            baseH[pf] = eH;
+        }
+        ++level;
+
+        while (nF + nH > 0) {
+            if (r + 2 >= a.max_round) {
+                if (leader) ctl->overflow = 1;
+                return;
+            }
+            ++rounds;
+            const Round rd{r};
+            const int pn = (r + 1) & 1;
+            if (leader) a.level_of[r + 1] = k;
+            const Sinks sk{a.F[fi ^ 1], a.H[fi ^ 1], Wout, &ctl->cntF[pn], &ctl->cntH[pn],
+                           &ctl->cntW[wp], baseF[pn], baseH[pn], baseW[wp], thr, bound};
+            process_list<TL>(a, rd, a.F[fi], nF, gwarp, nwarps, sk);
+            process_list<TL>(a, rd, a.H[fi], nH, gwarp, nwarps, sk);
+            if (!grid_sync(ctl, &epoch, a.spin_ns, &s_ok)) return;
+            const unsigned long long eF = ld_vol(&ctl->cntF[pn]), eH = ld_vol(&ctl->cntH[pn]);
+            n_alive -= nF + nH;
+            nF = (int64_t)(eF - baseF[pn]);
+            nH = (int64_t)(eH - baseH[pn]);
+            baseF[pn] = eF;
+            baseH[pn] = eH;
+            fi ^= 1;
+            ++r;
+            // compact the rows once half of their entries are removed edges
+            if (!TL && 4 * n_alive < nnz) {
+                ++compactions;
+                const Round now{r};
+                for (int64_t row = gwarp; row < a.n; row += nwarps) {
+                    const int64_t b = a.rowptr[row];
+                    const int32_t len = ld_cg(a.rowlen + row);
+                    int32_t wpos = 0;
+                    for (int32_t c = 0; c < len; c += 32) {
+                        const int32_t i = c + lane;
+                        bool keep = false;
+                        int32_t cv = 0, ev = 0;
+                        if (i < len) {
+                            ev = ld_cg(a.eid + b + i);
+                            cv = ld_cg(a.col + b + i);
+                            keep = !now.removed(ld_cg(a.t + ev));
+                        }
+                        const unsigned msk = __ballot_sync(0xffffffffu, keep);
+                        if (keep) {
+                            const int32_t q = wpos + __popc(msk & lanemask_lt());
+                            a.col[b + q] = cv;
+                            a.eid[b + q] = ev;
+                        }
+                        wpos += __popc(msk);
+                    }
+                    if (lane == 0) a.rowlen[row] = wpos;
+                }
+                if (!grid_sync(ctl, &epoch, a.spin_ns, &s_ok)) return;
+                nnz = 2 * n_alive;
+            }
+        }
+        // every append to this level's window list happened before the last
+        // barrier; the next level appends to the other counter
+        {
+            const unsigned long long eW = ld_vol(&ctl->cntW[wp]);
+            nW = (int64_t)(eW - baseW[wp]);
+            baseW[wp] = eW;
+            wi ^= 1;
+        }
+        // round r's frontier was empty; the next scan takes a fresh round number
+        ++r;
+        if (a.single) break;
+        if (n_alive == 0) break;
+        kmax = k;
+        ++k;
+    }
+    if (leader) {
+        ctl->kmax = kmax;
+        ctl->n_alive = n_alive;
+        ctl->rounds = rounds;
+        ctl->compactions = compactions;
+        ctl->full_scans = fulls;
     }
 }
 
-// Round end: remove the frontier (state = value), mark the next frontier.
-__global__ void k_finalize(const int32_t* __restrict__ F, unsigned nF, int32_t value,
-                           const int32_t* __restrict__ Fn, const unsigned* __restrict__ nFn,
-                           int32_t* __restrict__ t) {
+__global__ void k_peel_init(const int64_t* __restrict__ rowptr, int32_t n,
+                            int32_t* __restrict__ rowlen) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (int64_t i = i0; i < (int64_t)nF; i += stride) t[F[i]] = value;
-    const int64_t nn = *nFn;
-    for (int64_t i = i0; i < nn; i += stride) t[Fn[i]] = -1;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride)
+        rowlen[r] = (int32_t)(rowptr[r + 1] - rowptr[r]);
 }
 
+// Final states -> outputs: the k-truss mask (alive = 0) or truss numbers
+// (an edge removed in a round of level k has truss number k - 1).
 __global__ void k_mask_from_state(const int32_t* __restrict__ t, int64_t m,
                                   uint8_t* __restrict__ mask) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -131,87 +434,13 @@ __global__ void k_mask_from_state(const int32_t* __restrict__ t, int64_t m,
         mask[e] = t[e] == 0 ? 1 : 0;
 }
 
-inline unsigned blocks_for_warps(int64_t items) {
-    const int64_t warps_per_block = PL_THREADS / 32;
-    int64_t b = (items + warps_per_block - 1) / warps_per_block;
-    const int64_t cap = (int64_t)num_sms() * 16;
-    if (b < 1) b = 1;
-    return (unsigned)std::min(b, cap);
-}
-
-inline unsigned blocks_for_items(int64_t items) {
-    int64_t b = (items + PL_THREADS - 1) / PL_THREADS;
-    const int64_t cap = (int64_t)num_sms() * 16;
-    if (b < 1) b = 1;
-    return (unsigned)std::min(b, cap);
-}
-
-// Working buffers of a peel.
-struct PeelState {
-    int32_t* s = nullptr;      // support within the current subgraph
-    int32_t* t = nullptr;      // edge state
-    int32_t* alive[2] = {nullptr, nullptr};
-    int32_t* F = nullptr;
-    int32_t* Fn = nullptr;
-    unsigned* counters = nullptr;  // [0] alive out, [1] |F|, [2] |Fn|
-    int64_t n_alive = 0;
-    int cur = 0;
-    bool first = true;
-};
-
-int alloc_state(Scratch& sc, Graph* g, PeelState* ps, cudaStream_t s) {
-    const int64_t m = g->m;
-    TC_TRY(sc.alloc(&ps->s, m));
-    TC_TRY(sc.alloc(&ps->alive[0], m));
-    TC_TRY(sc.alloc(&ps->alive[1], m));
-    TC_TRY(sc.alloc(&ps->F, m));
-    TC_TRY(sc.alloc(&ps->Fn, m));
-    TC_TRY(sc.alloc(&ps->counters, 4));
-    TC_CUDA_TRY(
-        cudaMemcpyAsync(ps->s, g->support, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
-    TC_CUDA_TRY(cudaMemsetAsync(ps->t, 0, sizeof(int32_t) * m, s));
-    ps->n_alive = m;
-    return TC_OK;
-}
-
-// Peels one level: removes edges until every alive edge has s >= k - 2.
-// Removed edges get state `value`.  Updates ps->n_alive.
-int peel_level(Graph* g, PeelState* ps, int32_t k, int32_t value, cudaStream_t s) {
-    const int32_t thr = k - 2;
-    unsigned h[3];
-    TC_CUDA_TRY(cudaMemsetAsync(ps->counters, 0, sizeof(unsigned) * 3, s));
-    const int32_t* in = ps->first ? nullptr : ps->alive[ps->cur];
-    int32_t* out = ps->alive[ps->cur ^ 1];
-    k_level_scan<<<blocks_for_items(ps->n_alive), PL_THREADS, 0, s>>>(
-        in, ps->n_alive, ps->t, ps->s, thr, out, ps->counters + 0, ps->F, ps->counters + 1);
-    TC_LAUNCH_CHECK("k_level_scan");
-    TC_CUDA_TRY(cudaMemcpyAsync(h, ps->counters, sizeof(unsigned) * 2, cudaMemcpyDeviceToHost, s));
-    TC_CUDA_TRY(cudaStreamSynchronize(s));
-    ps->first = false;
-    ps->cur ^= 1;
-    int64_t n_alive = h[0];
-    unsigned nF = h[1];
-    int32_t* F = ps->F;
-    int32_t* Fn = ps->Fn;
-    int64_t rounds = 0;
-    while (nF > 0) {
-        if (++rounds > g->m + 1) return fail(TC_ETIMEDOUT, "peel: round limit exceeded");
-        TC_CUDA_TRY(cudaMemsetAsync(ps->counters + 2, 0, sizeof(unsigned), s));
-        k_peel_round<<<blocks_for_warps(nF), PL_THREADS, 0, s>>>(
-            F, nF, g->ends, g->rowptr, g->col, g->eid, ps->t, ps->s, thr, Fn, ps->counters + 2);
-        TC_LAUNCH_CHECK("k_peel_round");
-        k_finalize<<<blocks_for_items(std::max<int64_t>(nF, 1024)), PL_THREADS, 0, s>>>(
-            F, nF, value, Fn, ps->counters + 2, ps->t);
-        TC_LAUNCH_CHECK("k_finalize");
-        TC_CUDA_TRY(
-            cudaMemcpyAsync(&h[2], ps->counters + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-        TC_CUDA_TRY(cudaStreamSynchronize(s));
-        n_alive -= nF;
-        nF = h[2];
-        std::swap(F, Fn);
+__global__ void k_truss_from_state(int32_t* __restrict__ t, int64_t m,
+                                   const int32_t* __restrict__ level_of) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int32_t st = t[e];
+        t[e] = st < 0 ? level_of[-st] - 1 : 0;
     }
-    ps->n_alive = n_alive;
-    return TC_OK;
 }
 
 int ensure_support(Graph* g, cudaStream_t s) {
@@ -224,6 +453,94 @@ int ensure_support(Graph* g, cudaStream_t s) {
     return TC_OK;
 }
 
+inline unsigned small_grid(int64_t items) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * 8,
+                                                            (items + 255) / 256));
+}
+
+// Runs the persistent peel.  t (m entries, device) receives the edge states.
+// The triangle-list form is used when the lists (3T pairs of edge ids) fit
+// comfortably in free device memory, unless a test hook forces a form.
+int run_peel(Graph* g, int32_t k_first, bool single, int32_t* t, PeelCtl* result,
+             cudaStream_t s) {
+    const int64_t m = g->m;
+    TC_TRY(ensure_support(g, s));
+    Scratch sc(s);
+    PeelArgs a{};
+    a.m = m;
+    a.n = g->n;
+    a.ends = g->ends;
+    a.rowptr = g->rowptr;
+    a.t = t;
+    a.k_first = k_first;
+    a.single = single ? 1 : 0;
+    a.spin_ns = spin_limit_ns();
+
+    const int forced = peel_mode();
+    bool tl = false;
+    // list positions are 32-bit: the triangle-list form needs 3T < 2^32
+    if (triangle_lists_supported(g) && forced != PEEL_INTERSECT &&
+        3 * g->triangles < 0xffffffffLL) {
+        const double need = 24.0 * (double)g->triangles + 16.0 * (double)(m + 1);
+        size_t free_b = 0, total_b = 0;
+        TC_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        tl = forced == PEEL_LISTS || need < 0.6 * (double)free_b;
+    }
+    g->last_peel_lists = tl;
+    if (tl) {
+        unsigned long long* off;
+        int2* pairs;
+        TC_TRY(sc.alloc(&off, m + 1));
+        TC_TRY(sc.alloc(&pairs, std::max<int64_t>(1, 3 * g->triangles)));
+        TC_TRY(build_triangle_lists(g, g->support, off, pairs, s));
+        a.off = off;
+        a.pairs = pairs;
+    } else {
+        TC_TRY(sc.alloc(&a.rowlen, g->n));
+        TC_TRY(sc.alloc(&a.col, 2 * m));
+        TC_TRY(sc.alloc(&a.eid, 2 * m));
+        TC_CUDA_TRY(cudaMemcpyAsync(a.col, g->col, sizeof(int32_t) * 2 * m,
+                                    cudaMemcpyDeviceToDevice, s));
+        TC_CUDA_TRY(cudaMemcpyAsync(a.eid, g->eid, sizeof(int32_t) * 2 * m,
+                                    cudaMemcpyDeviceToDevice, s));
+        k_peel_init<<<small_grid(g->n), 256, 0, s>>>(g->rowptr, g->n, a.rowlen);
+        TC_LAUNCH_CHECK("k_peel_init");
+    }
+    TC_TRY(sc.alloc(&a.s, m));
+    for (int i = 0; i < 2; ++i) {
+        TC_TRY(sc.alloc(&a.A[i], m));
+        TC_TRY(sc.alloc(&a.W[i], m));
+        TC_TRY(sc.alloc(&a.F[i], m));
+        TC_TRY(sc.alloc(&a.H[i], m));
+    }
+    TC_TRY(sc.alloc(&a.ctl, 1));
+    a.max_round = 2 * m + 16;
+    if (a.max_round > 0x7fffffffLL) return fail(TC_EOVERFLOW, "peel: more than 2^30 edges");
+    TC_TRY(sc.alloc(&a.level_of, a.max_round));
+    TC_CUDA_TRY(cudaMemcpyAsync(a.s, g->support, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
+    TC_CUDA_TRY(cudaMemsetAsync(t, 0, sizeof(int32_t) * m, s));
+    TC_CUDA_TRY(cudaMemsetAsync(a.ctl, 0, sizeof(PeelCtl), s));
+
+    const void* fn = tl ? (const void*)k_peel<true> : (const void*)k_peel<false>;
+    int per_sm = 0;
+    TC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PK_THREADS, 0));
+    if (per_sm < 1) return fail(TC_ECUDA, "k_peel cannot be resident");
+    const int blocks = num_sms() * std::min(per_sm, 2);
+    void* params[] = {&a};
+    TC_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(PK_THREADS), params, 0, s));
+    count_launch();
+    TC_CUDA_TRY(cudaMemcpyAsync(result, a.ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, s));
+    TC_CUDA_TRY(cudaStreamSynchronize(s));
+    g->last_peel_rounds = result->rounds;
+    if (result->abort) return fail(TC_ETIMEDOUT, "peel: a grid barrier wait ran out of time");
+    if (result->overflow) return fail(TC_EOVERFLOW, "peel: round table exhausted");
+    if (!single) {
+        k_truss_from_state<<<small_grid(m), 256, 0, s>>>(t, m, a.level_of);
+        TC_LAUNCH_CHECK("k_truss_from_state");
+    }
+    return TC_OK;
+}
+
 }  // namespace
 
 int peel_ktruss(Graph* g, int32_t k, uint8_t* mask, int64_t* edges_left, cudaStream_t s) {
@@ -232,38 +549,25 @@ int peel_ktruss(Graph* g, int32_t k, uint8_t* mask, int64_t* edges_left, cudaStr
         if (edges_left) *edges_left = 0;
         return TC_OK;
     }
-    TC_TRY(ensure_support(g, s));
     Scratch sc(s);
-    PeelState ps;
-    TC_TRY(sc.alloc(&ps.t, m));
-    TC_TRY(alloc_state(sc, g, &ps, s));
-    TC_TRY(peel_level(g, &ps, k, 1, s));
-    k_mask_from_state<<<blocks_for_items(m), PL_THREADS, 0, s>>>(ps.t, m, mask);
+    int32_t* t;
+    TC_TRY(sc.alloc(&t, m));
+    PeelCtl r{};
+    TC_TRY(run_peel(g, k, true, t, &r, s));
+    k_mask_from_state<<<small_grid(m), 256, 0, s>>>(t, m, mask);
     TC_LAUNCH_CHECK("k_mask_from_state");
-    if (edges_left) *edges_left = ps.n_alive;
+    if (edges_left) *edges_left = r.n_alive;
     return TC_OK;
 }
 
 int peel_decompose(Graph* g, int32_t* truss, int32_t* kmax, cudaStream_t s) {
-    const int64_t m = g->m;
-    if (m == 0) {
+    if (g->m == 0) {
         *kmax = 0;
         return TC_OK;
     }
-    TC_TRY(ensure_support(g, s));
-    Scratch sc(s);
-    PeelState ps;
-    ps.t = truss;
-    TC_TRY(alloc_state(sc, g, &ps, s));
-    int32_t k = 3;
-    int32_t best = 2;
-    for (;;) {
-        TC_TRY(peel_level(g, &ps, k, k - 1, s));
-        if (ps.n_alive == 0) break;
-        best = k;
-        ++k;
-    }
-    *kmax = best;
+    PeelCtl r{};
+    TC_TRY(run_peel(g, 3, false, truss, &r, s));
+    *kmax = r.kmax;
     return TC_OK;
 }
 

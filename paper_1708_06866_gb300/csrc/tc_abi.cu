@@ -19,7 +19,12 @@ thread_local std::string t_last_error;
 std::atomic<int64_t> g_fail_alloc{0};
 std::atomic<int64_t> g_spin_ns{2000000000LL};
 std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_peel_mode{0};
+std::atomic<int> g_intersect_mode{0};
 }  // namespace
+
+int peel_mode() { return g_peel_mode.load(); }
+int intersect_mode() { return g_intersect_mode.load(); }
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
@@ -30,8 +35,28 @@ int fail(int code, const std::string& what) {
 
 int64_t spin_limit_ns() { return g_spin_ns.load(); }
 
+// The library allocates from the device's default stream-ordered pool.  Its
+// release threshold is raised once per device so that memory freed by one
+// call is kept for the next instead of being unmapped at every
+// synchronisation (the peel's scratch runs to gigabytes).
+void keep_pool_memory() {
+    static std::atomic<unsigned long long> done_mask{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return;
+    const unsigned long long bit = 1ull << dev;
+    if (done_mask.load() & bit) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        unsigned long long keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done_mask.fetch_or(bit);
+}
+
 int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
+    keep_pool_memory();
     int64_t c = g_fail_alloc.load();
     while (c > 0) {
         if (g_fail_alloc.compare_exchange_weak(c, c - 1)) {
@@ -283,6 +308,8 @@ int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream) {
     const int64_t m = gg->m, n = gg->n;
     info->device_bytes = m * (4 + 4 + 8 + 4 + 4 + 4) + 8 * (n + 1) + 8 * n +
                          (gg->support ? 4 * m : 0);
+    info->peel_rounds = gg->last_peel_rounds;
+    info->peel_lists = gg->last_peel_lists ? 1 : 0;
     return TC_OK;
 }
 
@@ -313,6 +340,16 @@ const char* tc_strerror(int code) {
 const char* tc_last_error(void) { return tc::t_last_error.c_str(); }
 
 int64_t tc_debug_fail_alloc(int64_t nth) { return tc::g_fail_alloc.exchange(nth < 0 ? 0 : nth); }
+
+int tc_debug_intersect_mode(int mode) {
+    if (mode < 0 || mode > 2) return tc::g_intersect_mode.load();
+    return tc::g_intersect_mode.exchange(mode);
+}
+
+int tc_debug_peel_mode(int mode) {
+    if (mode < 0 || mode > 2) return tc::g_peel_mode.load();
+    return tc::g_peel_mode.exchange(mode);
+}
 
 int64_t tc_debug_spin_limit_ns(int64_t ns) {
     if (ns <= 0) return tc::g_spin_ns.load();

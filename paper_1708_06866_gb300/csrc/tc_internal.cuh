@@ -46,6 +46,13 @@ enum : int {
 
 int64_t spin_limit_ns();
 
+// Which form of the peel to use (test hook; PEEL_AUTO by default).
+enum : int { PEEL_AUTO = 0, PEEL_LISTS = 1, PEEL_INTERSECT = 2 };
+int peel_mode();
+// Which count/support kernel to use (test hook): 0 automatic, 1 row/hash
+// kernel where the graph allows it, 2 edge-per-warp binary search.
+int intersect_mode();
+
 // ---------------------------------------------------------------- memory
 
 // Stream-ordered device allocation with the fault-injection hook.
@@ -59,12 +66,14 @@ int dev_alloc_n(T** p, int64_t count, cudaStream_t s) {
 
 // RAII holder for scratch buffers freed (stream-ordered) at scope exit.
 struct Scratch {
+    static constexpr int kMax = 48;
     cudaStream_t s;
-    void* ptrs[32];
+    void* ptrs[kMax];
     int n = 0;
     explicit Scratch(cudaStream_t st) : s(st) {}
     template <typename T>
     int alloc(T** p, int64_t count) {
+        if (n == kMax) return fail(TC_ENOMEM, "internal: too many scratch buffers");
         int rc = dev_alloc_n(p, count, s);
         if (rc == TC_OK) ptrs[n++] = *p;
         return rc;
@@ -197,6 +206,8 @@ struct Graph {
     int32_t max_out = 0;      // max |N+(u)|
     int32_t max_deg = 0;
     int64_t wedge_work = -1;  // sum of |N+(u)| + |N+(v)| over oriented edges (lazy)
+    int64_t last_peel_rounds = 0;  // bulk rounds of the most recent peel
+    bool last_peel_lists = false;  // whether it used triangle lists
     // cached support (edge-id order) and triangle count
     int32_t* support = nullptr;
     bool support_valid = false;
@@ -212,6 +223,9 @@ int compute_support(Graph* g, int32_t* s_out_dev, bool want_support, int64_t* tr
                     cudaStream_t s);
 int peel_ktruss(Graph* g, int32_t k, uint8_t* mask_dev, int64_t* edges_left, cudaStream_t s);
 int graph_wedge_work(Graph* g, int64_t* out, cudaStream_t s);
+bool triangle_lists_supported(const Graph* g);
+int build_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off, int2* pairs,
+                         cudaStream_t s);
 int peel_decompose(Graph* g, int32_t* truss_dev, int32_t* kmax, cudaStream_t s);
 
 }  // namespace tc

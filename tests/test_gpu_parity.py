@@ -31,16 +31,40 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
 
 
+PEEL_MODES = {"lists": 1, "intersect": 2}
+
+
 def gpu_all(src, dst, n, ks=(2, 3, 4, 5, 6)):
+    """Every ABI call on one graph; the peel runs in both of its forms."""
     g = tc.tc_build_csr(dev(src), dev(dst), n)
     lo, hi = tc.tc_edges(g)
+    # the edge-per-warp kernel first, then the default (row kernel), whose
+    # supports the peel then reuses
+    prev = tc.tc_debug_intersect_mode(2)
+    try:
+        T_warp = tc.tc_count(g)
+        s_warp, _ = tc.tc_edge_support(g)
+        s_warp = s_warp.cpu().numpy()
+    finally:
+        tc.tc_debug_intersect_mode(prev)
     T = tc.tc_count(g)
     s, T2 = tc.tc_edge_support(g)
-    masks = {k: tc.ktruss(g, k) for k in ks}
-    kmax, truss = tc.ktruss_max(g)
     out = dict(m=g.m, lo=lo.cpu().numpy(), hi=hi.cpu().numpy(), T=T, T2=T2,
-               s=s.cpu().numpy(), masks={k: (mk.cpu().numpy(), c) for k, (mk, c) in masks.items()},
-               kmax=kmax, truss=truss.cpu().numpy())
+               s=s.cpu().numpy(), peel={}, T_warp=T_warp, s_warp=s_warp)
+    for name, mode in PEEL_MODES.items():
+        prev = tc.tc_debug_peel_mode(mode)
+        try:
+            masks = {}
+            for k in ks:
+                mk, c = tc.ktruss(g, k)
+                masks[k] = (mk.cpu().numpy(), c)
+            kmax, truss = tc.ktruss_max(g)
+            info = tc.tc_graph_info(g)
+        finally:
+            tc.tc_debug_peel_mode(prev)
+        if g.m:
+            assert info["peel_lists"] == (1 if name == "lists" else 0)
+        out["peel"][name] = dict(masks=masks, kmax=kmax, truss=truss.cpu().numpy())
     tc.tc_graph_free(g)
     return out
 
@@ -51,16 +75,21 @@ def check(src, dst, n, ks=(2, 3, 4, 5, 6)):
     assert got["m"] == og.m
     assert np.array_equal(got["lo"], og.lo) and np.array_equal(got["hi"], og.hi)
     T = og.count()
-    assert got["T"] == T and got["T2"] == T
+    assert got["T"] == T and got["T2"] == T and got["T_warp"] == T
     assert np.array_equal(got["s"], og.support())
-    for k in ks:
-        mask, sup, left = og.ktruss(k)
-        gm, gc = got["masks"][k]
-        assert np.array_equal(gm, mask), f"k={k}"
-        assert gc == left, f"k={k}"
+    assert np.array_equal(got["s_warp"], got["s"])
     kmax, truss = og.truss_decomposition()
-    assert got["kmax"] == kmax
-    assert np.array_equal(got["truss"], truss)
+    for name, res in got["peel"].items():
+        for k in ks:
+            mask, sup, left = og.ktruss(k)
+            gm, gc = res["masks"][k]
+            assert np.array_equal(gm, mask), f"{name} k={k}"
+            assert gc == left, f"{name} k={k}"
+        assert res["kmax"] == kmax, name
+        assert np.array_equal(res["truss"], truss), name
+    got["masks"] = got["peel"]["lists"]["masks"]
+    got["kmax"] = got["peel"]["lists"]["kmax"]
+    got["truss"] = got["peel"]["lists"]["truss"]
     return got
 
 
@@ -257,7 +286,32 @@ def test_rmat20_full_size_against_stored_oracle():
         mask, c = tc.ktruss(g, int(k))
         assert c == int(left)
         assert _sha(mask.cpu().numpy().astype(np.int32)) == h
+    for mode in PEEL_MODES.values():
+        prev = tc.tc_debug_peel_mode(mode)
+        try:
+            kmax, truss = tc.ktruss_max(g)
+        finally:
+            tc.tc_debug_peel_mode(prev)
+        assert kmax == int(fx["kmax"][0][0])
+        assert _sha(truss.cpu().numpy()) == fx["truss_sha256"][0][0]
+    g.free()
+
+
+def test_bounded_wait_expiry_is_reported():
+    """A device-side wait that runs out returns TC_ETIMEDOUT and leaves the
+    graph and the context usable (the waits are bounded; nothing faults)."""
+    s, d, n = graphgen.rmat(12, seed=21)
+    g = tc.tc_build_csr(dev(s), dev(d), n)
+    og = oracle.OracleGraph.from_edges(s, d, n)
+    old = tc.tc_debug_spin_limit_ns(1)
+    try:
+        with pytest.raises(tc.TCError) as ei:
+            tc.ktruss_max(g)
+        assert ei.value.code == tc.TC_ETIMEDOUT
+    finally:
+        tc.tc_debug_spin_limit_ns(old)
     kmax, truss = tc.ktruss_max(g)
-    assert kmax == int(fx["kmax"][0][0])
-    assert _sha(truss.cpu().numpy()) == fx["truss_sha256"][0][0]
+    assert kmax == og.truss_decomposition()[0]
+    assert np.array_equal(truss.cpu().numpy(), og.truss_decomposition()[1])
+    assert tc.tc_graph_info(g)["peel_rounds"] > 0
     g.free()
