@@ -63,6 +63,8 @@ def _bind(lib):
     lib.oracle_support_of.restype = None
     lib.oracle_support_within.argtypes = [vp, u8p, i32p]
     lib.oracle_support_within.restype = None
+    lib.oracle_support_within_of.argtypes = [vp, u8p, i64p, ctypes.c_int64, i32p]
+    lib.oracle_support_within_of.restype = None
     lib.oracle_ktruss.argtypes = [vp, ctypes.c_int32, u8p, i32p]
     lib.oracle_ktruss.restype = ctypes.c_int64
     lib.oracle_truss_decomposition.argtypes = [vp, i32p]
@@ -159,6 +161,16 @@ class OracleGraph:
         s = np.empty(self.m, dtype=np.int32)
         self._lib.oracle_support_within(self._h, _ptr(mk, ctypes.c_uint8),
                                         _ptr(s, ctypes.c_int32))
+        return s
+
+    def support_within_of(self, mask, edges) -> np.ndarray:
+        """For the listed edge ids: triangles through the edge whose two other edges are in mask."""
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        e = np.ascontiguousarray(edges, dtype=np.int64)
+        s = np.empty(len(e), dtype=np.int32)
+        self._lib.oracle_support_within_of(self._h, _ptr(mk, ctypes.c_uint8),
+                                           _ptr(e, ctypes.c_int64), len(e),
+                                           _ptr(s, ctypes.c_int32))
         return s
 
     def ktruss(self, k: int):

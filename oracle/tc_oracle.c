@@ -249,6 +249,30 @@ void oracle_support_within(const oracle_graph* g, const uint8_t* alive, int32_t*
     }
 }
 
+/* For the listed edges only: the number of triangles through the edge whose
+ * two other edges have alive[] != 0, whatever the edge's own flag.  For an
+ * edge of a k-truss this is its support within the truss; for an edge
+ * outside the (maximal) k-truss it must be below k - 2, or the truss plus
+ * that edge would be a larger k-truss. */
+void oracle_support_within_of(const oracle_graph* g, const uint8_t* alive, const int64_t* edges,
+                              int64_t cnt, int32_t* s) {
+    const int64_t dmax = max_degree(g) + 1;
+    int64_t* pa = (int64_t*)malloc(sizeof(int64_t) * (size_t)dmax);
+    int64_t* pb = (int64_t*)malloc(sizeof(int64_t) * (size_t)dmax);
+    for (int64_t i = 0; i < cnt; ++i) {
+        const int64_t e = edges[i];
+        int32_t c = 0;
+        if (e >= 0 && e < g->m) {
+            const int64_t k = common(g, g->lo[e], g->hi[e], pa, pb);
+            for (int64_t j = 0; j < k; ++j)
+                if (alive[g->eid[pa[j]]] && alive[g->eid[pb[j]]]) ++c;
+        }
+        s[i] = c;
+    }
+    free(pa);
+    free(pb);
+}
+
 /* One peeling level: starting from the edges with alive[e] != 0 and their
  * current supports s[], remove edges whose support is below k - 2 until
  * none is.  Removing e = {a, b} destroys each triangle {a, b, w} whose other

@@ -371,3 +371,24 @@ def test_support_invariant_on_rmat():
     s, d, n = graphgen.rmat(12, seed=1)
     g = oracle.OracleGraph.from_edges(s, d, n)
     assert g.support().sum() == 3 * g.count()
+
+
+def test_support_within_of_matches_full_version():
+    s, d, n = graphgen.rmat(10, seed=3)
+    g = oracle.OracleGraph.from_edges(s, d, n)
+    mask, sup, _ = g.ktruss(5)
+    sel = np.arange(0, g.m, 7)
+    assert np.array_equal(g.support_within_of(mask, sel), g.support_within(mask)[sel])
+    assert np.array_equal(g.support_within_of(mask, sel), sup[sel])
+
+
+def test_edges_outside_a_truss_close_too_few_triangles_with_it():
+    """Maximality of the k-truss (Section III-B): an edge outside it closes
+    fewer than k - 2 triangles with truss edges."""
+    s, d, n = graphgen.rmat(11, seed=4)
+    g = oracle.OracleGraph.from_edges(s, d, n)
+    for k in (3, 4, 6, 8):
+        mask, _, _ = g.ktruss(k)
+        out = np.flatnonzero(mask == 0)
+        if len(out):
+            assert (g.support_within_of(mask, out) < k - 2).all()
