@@ -377,7 +377,7 @@ def test_support_within_of_matches_full_version():
     s, d, n = graphgen.rmat(10, seed=3)
     g = oracle.OracleGraph.from_edges(s, d, n)
     mask, sup, _ = g.ktruss(5)
-    sel = np.arange(0, g.m, 7)
+    sel = np.flatnonzero(mask)[::7]
     assert np.array_equal(g.support_within_of(mask, sel), g.support_within(mask)[sel])
     assert np.array_equal(g.support_within_of(mask, sel), sup[sel])
 
