@@ -110,8 +110,12 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ our arm
 
-def run_step(tc, torch, src, dst, n, wl, stream, ev=None, outs=None):
-    """One pass of the path; returns (m, triangles, kmax or truss counts)."""
+def run_step(tc, torch, src, dst, n, wl, stream, ev=None, outs=None, infos=None):
+    """One pass of the path.  Returns (m, triangles, truss results).
+
+    Events (if ev is a list) mark the phases on the stream; the graph's
+    per-kernel device times are collected into infos after the last event.
+    """
     def mark(name):
         if ev is not None:
             e = torch.cuda.Event(enable_timing=True)
@@ -130,16 +134,51 @@ def run_step(tc, torch, src, dst, n, wl, stream, ev=None, outs=None):
         for k in wl.truss_ks:
             mk_out = outs.get(f"mask{k}") if outs else None
             _, res[k] = tc.ktruss(g, k, out=mk_out, stream=stream)
+            if infos is not None:   # one peel launch per k
+                inf = tc.tc_graph_info(g)
+                infos.append({"peel_kernel_ns": inf["peel_kernel_ns"],
+                              "peel_bytes": inf["peel_bytes"]})
         mark("truss")
     elif wl.name != "er4096":
         tr_out = outs.get("truss") if outs else None
         res["kmax"], _ = tc.ktruss_max(g, out=tr_out, stream=stream)
         mark("truss")
+    if infos is not None:
+        inf = tc.tc_graph_info(g)
+        if wl.truss_ks:
+            inf["peel_kernel_ns"] = None
+        infos.append(inf)
     m = g.m
     g.free()
-    mark("free")
     assert T == T2
     return m, T, res
+
+
+def kernel_rooflines(infos, count_bytes, support_bytes, lists_bytes, peak):
+    """Per main kernel: launches, mean device time, algorithmic bytes, GB/s."""
+    acc = {}
+    for inf in infos:
+        for name, tkey, nbytes in (
+                ("masked product, count (k_rows<COUNT>)", "count_kernel_ns", count_bytes),
+                ("masked product, support (k_rows<SUPPORT>)", "support_kernel_ns", support_bytes),
+                ("triangle lists (k_rows<LISTS>)", "lists_kernel_ns", lists_bytes),
+                ("peel (k_peel)", "peel_kernel_ns", inf.get("peel_bytes"))):
+            t = inf.get(tkey)
+            if t is None or t <= 0:
+                continue
+            a = acc.setdefault(name, {"launch_ns": [], "bytes": []})
+            a["launch_ns"].append(t)
+            a["bytes"].append(nbytes)
+    out = {}
+    for name, a in acc.items():
+        ns = float(np.mean(a["launch_ns"]))
+        b = float(np.mean(a["bytes"]))
+        gbs = b / ns  # bytes per ns == GB/s
+        out[name] = {"launches": len(a["launch_ns"]), "ms_per_launch": round(ns / 1e6, 3),
+                     "bytes_per_launch": int(b), "achieved_gbs": round(gbs, 1),
+                     "frac": round(gbs / peak, 4),
+                     "total_ms": round(ns * len(a["launch_ns"]) / 1e6, 3)}
+    return out
 
 
 def bench_ours(args, rank, world):
@@ -161,12 +200,19 @@ def bench_ours(args, rank, world):
     flush = torch.empty(args.flush_mb << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
 
-    # graph sizes and the algorithmic bytes of the intersection kernel
+    # graph sizes and the algorithmic bytes of the masked-product kernels:
+    # every list entry they merge (4 B), the row offsets (8 B per vertex),
+    # the edge ids of the oriented edges (4 B); support adds a 4-B write per
+    # edge; the triangle-list build adds the 8-B pair written per incidence
     g = tc.tc_build_csr(src, dst, n, stream=stream)
-    info = tc.tc_graph_info(g, stream=stream)
+    wedge = tc.tc_graph_wedge_work(g, stream=stream)
+    T0 = tc.tc_count(g, stream=stream)
+    info = tc.tc_graph_info(g)
     g.free()
     m = info["m"]
-    count_bytes = 4 * info["wedge_work"] + 8 * (n + 1) + 4 * m
+    count_bytes = 4 * wedge + 8 * (n + 1) + 4 * m
+    support_bytes = count_bytes + 4 * m
+    lists_bytes = count_bytes + 24 * T0
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -178,6 +224,7 @@ def bench_ours(args, rank, world):
 
     phases = {}
     step_ms = []
+    infos = []
     launches0 = tc.tc_launch_count()
     sampler = ClockSampler(local)
     with sampler:
@@ -185,7 +232,7 @@ def bench_ours(args, rank, world):
             for _ in range(args.steps):
                 flush.fill_(1)          # evict L2 between steps (outside the events)
                 ev = []
-                m_, T, res = run_step(tc, torch, src, dst, n, wl, stream, ev=ev)
+                m_, T, res = run_step(tc, torch, src, dst, n, wl, stream, ev=ev, infos=infos)
                 torch.cuda.synchronize()
                 step_ms.append(ev[0][1].elapsed_time(ev[-1][1]))
                 for (a, ea), (b, eb) in zip(ev[:-1], ev[1:]):
@@ -199,15 +246,17 @@ def bench_ours(args, rank, world):
     ms_per_step = total_ms / args.steps
     value = world * m * args.steps / (total_ms / 1e3)
 
-    # roofline of the intersection kernel: the count phase is one launch of it
-    # (plus an 8-byte reduction and read-back), timed on its stream in every step
-    count_ms = float(np.mean(phases["count"]))
+    # roofline of the dominant kernel: the library times each launch of its
+    # main kernels with CUDA events on the call's stream, in every timed step
     peak, peak_kind = load_peaks()
-    achieved = count_bytes / (count_ms / 1e3) / 1e9
-    roofline = {"kernel": "k_intersect_warp (tc_count)", "bound": "hbm",
-                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                "traffic": None, "algorithmic_bytes_per_launch": int(count_bytes)}
+    kernels = kernel_rooflines(infos, count_bytes, support_bytes, lists_bytes, peak)
+    dom_name, dom = max(kernels.items(), key=lambda kv: kv[1]["total_ms"])
+    roofline = {"kernel": dom_name, "bound": "hbm", "achieved": dom["achieved_gbs"],
+                "peak": peak, "unit": "GB/s", "frac": dom["frac"],
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind ==
+                "measured" else "fallback",
+                "traffic": None, "algorithmic_bytes_per_launch": dom["bytes_per_launch"],
+                "ms_per_launch": dom["ms_per_launch"]}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -216,11 +265,11 @@ def bench_ours(args, rank, world):
            "config": {"workload": wl.name, "description": wl.description, "n": n,
                       "m_in": info["m_in"], "m": m, "triangles": T,
                       "truss": res, "max_degree": info["max_degree"],
-                      "max_out_degree": info["max_out"], "wedge_work": info["wedge_work"],
+                      "max_out_degree": info["max_out"], "wedge_work": wedge,
                       "l2": f"flushed between steps ({args.flush_mb} MB write)",
                       "parallelism": "replicas" if world > 1 else "single"},
            "phases_ms": {k: round(float(np.mean(v)), 3) for k, v in phases.items()},
-           "roofline": roofline, "gpu_launches": launches,
+           "roofline": roofline, "kernels": kernels, "gpu_launches": launches,
            "clocks": sampler.summary()}
 
     if not args.no_e2e:

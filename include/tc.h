@@ -147,17 +147,35 @@ typedef struct {
     int64_t m;             /* undirected edges after cleaning */
     int64_t max_degree;    /* largest vertex degree */
     int64_t max_out;       /* largest out-degree |N+(u)| in the degree orientation */
-    int64_t wedge_work;    /* sum over oriented edges (u, v) of |N+(u)| + |N+(v)|:
-                              the list entries the masked product merges */
+    int64_t wedge_work;    /* sum over oriented edges (u, v) of |N+(u)| + |N+(v)|
+                              (the list entries a merge-based masked product
+                              reads), or -1 until tc_graph_wedge_work ran */
     int64_t device_bytes;  /* device memory held by the graph */
     int64_t peel_rounds;   /* bulk removal rounds of the most recent ktruss /
                               ktruss_max call on this graph (0 if none) */
     int64_t peel_lists;    /* 1 if that call read precomputed per-edge triangle
                               lists, 0 if it intersected neighbour lists */
+    /* Device time (CUDA events on the call's stream, ns; -1 = not run or not
+     * measured) of the latest launch on this graph of: the masked-product
+     * kernel of tc_count, that of tc_edge_support (measured when the call
+     * returns triangles), the triangle-list build and the peel kernel. */
+    int64_t count_kernel_ns;
+    int64_t support_kernel_ns;
+    int64_t lists_kernel_ns;
+    int64_t peel_kernel_ns;
+    int64_t peel_bytes;    /* algorithmic bytes of that peel launch: 12 per
+                              level-scan entry, 8 per triangle- or neighbour-list
+                              entry read, 4 per binary-search step and per edge
+                              state read, 8 per support decrement */
 } tc_graph_info_t;
 
-/* Fills *info (host pointer).  Synchronises the stream. */
+/* Fills *info (host pointer) from values the library already holds; launches
+ * nothing.  cuda_stream is unused. */
 int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream);
+
+/* Computes (once per graph, one kernel) the sum over oriented edges (u, v)
+ * of |N+(u)| + |N+(v)| into *out (host).  Synchronises the stream. */
+int tc_graph_wedge_work(tc_graph* g, int64_t* out, void* cuda_stream);
 
 /* Number of CUDA kernels the library has launched in this process (all
  * graphs, all threads); lets a caller count the launches of a region. */

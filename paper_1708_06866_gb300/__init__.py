@@ -29,7 +29,7 @@ from . import _build
 __all__ = [
     "TCError", "Graph", "load_library", "library_path", "tc_build_csr", "tc_count",
     "tc_edge_support", "ktruss", "ktruss_max", "tc_num_edges", "tc_num_vertices", "tc_edges",
-    "tc_graph_info", "tc_launch_count",
+    "tc_graph_info", "tc_graph_wedge_work", "tc_launch_count",
     "tc_graph_free", "tc_strerror", "tc_last_error", "tc_debug_fail_alloc",
     "tc_debug_spin_limit_ns", "tc_debug_peel_mode", "tc_debug_intersect_mode", "TC_OK", "TC_EINVAL", "TC_ERANGE", "TC_ENOMEM", "TC_ECUDA",
     "TC_ETIMEDOUT", "TC_EOVERFLOW", "TC_INPUT_AUTO", "TC_INPUT_DEVICE", "TC_INPUT_HOST",
@@ -73,6 +73,7 @@ def load_library(build_if_missing: bool = True):
             "tc_last_error": (ctypes.c_char_p, []),
             "tc_graph_info": (ctypes.c_int, [vp, ctypes.POINTER(GraphInfo), vp]),
             "tc_launch_count": (i64, []),
+            "tc_graph_wedge_work": (ctypes.c_int, [vp, ctypes.POINTER(i64), vp]),
             "tc_debug_fail_alloc": (i64, [i64]),
             "tc_debug_spin_limit_ns": (i64, [i64]),
             "tc_debug_peel_mode": (ctypes.c_int, [ctypes.c_int]),
@@ -90,7 +91,8 @@ class GraphInfo(ctypes.Structure):
     """Mirror of tc_graph_info_t."""
     _fields_ = [(f, ctypes.c_int64) for f in
                 ("n", "m_in", "m", "max_degree", "max_out", "wedge_work", "device_bytes",
-                 "peel_rounds", "peel_lists")]
+                 "peel_rounds", "peel_lists", "count_kernel_ns", "support_kernel_ns",
+                 "lists_kernel_ns", "peel_kernel_ns", "peel_bytes")]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -280,6 +282,14 @@ def tc_graph_info(g: Graph, stream=None) -> dict:
     _check(load_library().tc_graph_info(g.handle, ctypes.byref(info), _stream_handle(stream)),
            "tc_graph_info")
     return info.as_dict()
+
+
+def tc_graph_wedge_work(g: Graph, stream=None) -> int:
+    """Sum over oriented edges (u, v) of |N+(u)| + |N+(v)| (one kernel, cached)."""
+    out = ctypes.c_int64(0)
+    _check(load_library().tc_graph_wedge_work(g.handle, ctypes.byref(out), _stream_handle(stream)),
+           "tc_graph_wedge_work")
+    return out.value
 
 
 def tc_launch_count() -> int:

@@ -404,6 +404,8 @@ int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangle
     unsigned long long* partials;
     TC_TRY(sc.alloc(&partials, blocks));
     if (want_support) TC_CUDA_TRY(cudaMemsetAsync(sup, 0, sizeof(int32_t) * m, s));
+    KernelTimer timer;
+    TC_TRY(timer.start(s));
     if (rows) {
         if (want_support)
             TC_TRY(launch_rows<SUPPORT>(g, sup, nullptr, nullptr, partials, blocks, s));
@@ -417,6 +419,7 @@ int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangle
                                                           g->col, g->eid, m, nullptr, partials);
         TC_LAUNCH_CHECK("k_edges_warp");
     }
+    TC_TRY(timer.stop(s));
     k_reduce_partials<<<1, 1024, 0, s>>>(partials, blocks, g->dev_scalars);
     TC_LAUNCH_CHECK("k_reduce_partials");
     if (triangles) {
@@ -424,6 +427,7 @@ int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangle
         TC_CUDA_TRY(cudaMemcpyAsync(&t, g->dev_scalars, sizeof(t), cudaMemcpyDeviceToHost, s));
         TC_CUDA_TRY(cudaStreamSynchronize(s));
         *triangles = (int64_t)t;
+        (want_support ? g->stats.support_ns : g->stats.count_ns) = timer.elapsed_ns();
     }
     return TC_OK;
 }
@@ -459,7 +463,12 @@ int build_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off, 
     const int blocks = rows_blocks(g, LISTS);
     unsigned long long* partials;
     TC_TRY(sc.alloc(&partials, blocks));
+    KernelTimer timer;
+    TC_TRY(timer.start(s));
     TC_TRY(launch_rows<LISTS>(g, nullptr, cursor, pairs, partials, blocks, s));
+    TC_TRY(timer.stop(s));
+    TC_CUDA_TRY(cudaStreamSynchronize(s));
+    g->stats.lists_ns = timer.elapsed_ns();
     return TC_OK;
 }
 

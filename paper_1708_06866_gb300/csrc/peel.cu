@@ -49,6 +49,16 @@ struct PeelCtl {
     long long rounds;            // non-empty rounds
     long long compactions;
     long long full_scans;
+    unsigned long long scanned;   // level-scan entries read
+    unsigned long long entries;   // triangle-list entries (TL) or shorter-list entries (IX) read
+    unsigned long long searches;  // binary-search loads (IX)
+    unsigned long long lookups;   // edge-state loads while processing frontiers
+    unsigned long long lowered;   // support decrements
+};
+
+// Per-thread work counters, summed into PeelCtl at the end.
+struct Tally {
+    unsigned long long scanned = 0, entries = 0, searches = 0, lookups = 0, lowered = 0;
 };
 
 struct PeelArgs {
@@ -160,7 +170,9 @@ __device__ __forceinline__ bool is_heavy(const PeelArgs& a, int32_t e) {
 // its support falls from k - 2 to k - 3 and the window list when it falls to
 // just below the window bound (exactly one atomic sees each crossing).
 template <bool TL>
-__device__ __forceinline__ void lower(const PeelArgs& a, Round rd, int32_t x, const Sinks& k) {
+__device__ __forceinline__ void lower(const PeelArgs& a, Round rd, int32_t x, const Sinks& k,
+                                      Tally& tl) {
+    ++tl.lowered;
     const int old = atomicSub(a.s + x, 1);
     if (old == k.thr) {
         a.t[x] = -(rd.r + 1);
@@ -175,25 +187,48 @@ __device__ __forceinline__ void lower(const PeelArgs& a, Round rd, int32_t x, co
 // owns it and lowers the support of each of f, g that is not dying.
 template <bool TL>
 __device__ __forceinline__ void destroy(const PeelArgs& a, Round rd, int32_t e, int32_t f,
-                                        int32_t tf, int32_t g, int32_t tg, const Sinks& k) {
+                                        int32_t tf, int32_t g, int32_t tg, const Sinks& k,
+                                        Tally& tl) {
     if ((rd.dying(tf) && f < e) || (rd.dying(tg) && g < e)) return;
-    if (rd.alive(tf)) lower<TL>(a, rd, f, k);
-    if (rd.alive(tg)) lower<TL>(a, rd, g, k);
+    if (rd.alive(tf)) lower<TL>(a, rd, f, k, tl);
+    if (rd.alive(tg)) lower<TL>(a, rd, g, k, tl);
 }
 
-// All triangles through frontier edge e, by a group of gsize lanes.
+// All triangles through frontier edge e, by a group of gsize lanes.  The
+// edge's current support is exactly its number of live triangles (those
+// whose other two edges are not removed): support 0 means nothing to do,
+// and a single-warp group stops once it has seen them all.
 template <bool TL>
 __device__ __forceinline__ void process_edge(const PeelArgs& a, Round rd, int32_t e,
-                                             int64_t glane, int64_t gsize, const Sinks& k) {
+                                             int64_t glane, int64_t gsize, const Sinks& k,
+                                             Tally& tl) {
+    const int32_t live = ld_cg(a.s + e);
+    if (live <= 0) return;
+    const bool one_warp = gsize == 32;
+    int32_t seen = 0;  // live triangles met so far (one_warp only; warp-uniform)
     if (TL) {
         const int64_t q0 = (int64_t)a.off[e], q1 = (int64_t)a.off[e + 1];
-        for (int64_t q = q0 + glane; q < q1; q += gsize) {
-            const int2 fg = a.pairs[q];
-            const int32_t tf = ld_cg(a.t + fg.x);
-            if (rd.removed(tf)) continue;
-            const int32_t tg = ld_cg(a.t + fg.y);
-            if (rd.removed(tg)) continue;
-            destroy<TL>(a, rd, e, fg.x, tf, fg.y, tg, k);
+        for (int64_t cb = q0 + (glane & ~31ll); cb < q1; cb += gsize) {
+            const int64_t q = cb + (glane & 31);
+            bool found = false;
+            if (q < q1) {
+                ++tl.entries;
+                const int2 fg = a.pairs[q];
+                const int32_t tf = ld_cg(a.t + fg.x);
+                ++tl.lookups;
+                if (!rd.removed(tf)) {
+                    const int32_t tg = ld_cg(a.t + fg.y);
+                    ++tl.lookups;
+                    if (!rd.removed(tg)) {
+                        found = true;
+                        destroy<TL>(a, rd, e, fg.x, tf, fg.y, tg, k, tl);
+                    }
+                }
+            }
+            if (one_warp) {
+                seen += __popc(__ballot_sync(0xffffffffu, found));
+                if (seen >= live) break;
+            }
         }
         return;
     }
@@ -208,22 +243,38 @@ __device__ __forceinline__ void process_edge(const PeelArgs& a, Round rd, int32_
         sl = ll;
         ll = t1;
     }
-    for (int64_t p = glane; p < sl; p += gsize) {
-        const int32_t f = ld_cg(a.eid + s0 + p);
-        const int32_t tf = ld_cg(a.t + f);
-        if (rd.removed(tf)) continue;
-        const int32_t w = ld_cg(a.col + s0 + p);
-        int32_t lo = 0, hi = ll;
-        while (lo < hi) {
-            const int32_t mid = (lo + hi) >> 1;
-            if (ld_cg(a.col + l0 + mid) < w) lo = mid + 1;
-            else hi = mid;
+    for (int64_t cb = (glane & ~31ll); cb < sl; cb += gsize) {
+        const int64_t p = cb + (glane & 31);
+        bool found = false;
+        if (p < sl) {
+            ++tl.entries;
+            const int32_t f = ld_cg(a.eid + s0 + p);
+            const int32_t tf = ld_cg(a.t + f);
+            ++tl.lookups;
+            if (!rd.removed(tf)) {
+                const int32_t w = ld_cg(a.col + s0 + p);
+                int32_t lo = 0, hi = ll;
+                while (lo < hi) {
+                    const int32_t mid = (lo + hi) >> 1;
+                    ++tl.searches;
+                    if (ld_cg(a.col + l0 + mid) < w) lo = mid + 1;
+                    else hi = mid;
+                }
+                if (lo < ll && ld_cg(a.col + l0 + lo) == w) {
+                    const int32_t g = ld_cg(a.eid + l0 + lo);
+                    const int32_t tg = ld_cg(a.t + g);
+                    ++tl.lookups;
+                    if (!rd.removed(tg)) {
+                        found = true;
+                        destroy<TL>(a, rd, e, f, tf, g, tg, k, tl);
+                    }
+                }
+            }
         }
-        if (lo >= ll || ld_cg(a.col + l0 + lo) != w) continue;
-        const int32_t g = ld_cg(a.eid + l0 + lo);
-        const int32_t tg = ld_cg(a.t + g);
-        if (rd.removed(tg)) continue;
-        destroy<TL>(a, rd, e, f, tf, g, tg, k);
+        if (one_warp) {
+            seen += __popc(__ballot_sync(0xffffffffu, found));
+            if (seen >= live) break;
+        }
     }
 }
 
@@ -233,7 +284,7 @@ __device__ __forceinline__ void process_edge(const PeelArgs& a, Round rd, int32_
 template <bool TL>
 __device__ __forceinline__ void process_list(const PeelArgs& a, Round rd, const int32_t* L,
                                              int64_t nL, int64_t gwarp, int64_t nwarps,
-                                             const Sinks& k) {
+                                             const Sinks& k, Tally& tl) {
     if (nL == 0) return;
     int64_t W = 1;
     while (nL * (W * 2) <= nwarps) W *= 2;
@@ -242,7 +293,7 @@ __device__ __forceinline__ void process_list(const PeelArgs& a, Round rd, const 
     if (group >= ngroups) return;
     const int64_t glane = (gwarp % W) * 32 + (threadIdx.x & 31);
     for (int64_t j = group; j < nL; j += ngroups)
-        process_edge<TL>(a, rd, ld_cg(L + j), glane, 32 * W, k);
+        process_edge<TL>(a, rd, ld_cg(L + j), glane, 32 * W, k, tl);
 }
 
 // The peel.  Levels k = k_first, k_first + 1, ...; each level starts with a
@@ -282,6 +333,7 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
     int32_t r = 1;  // round whose frontier the next level scan collects
     int32_t bound = INT_MIN;
     int level = 0;
+    Tally tl;
 
     for (;;) {
         if (r + 2 >= a.max_round) {  // uniform: every block sees the same r
@@ -303,6 +355,7 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
                 bool alive = false, win = false, light = false, heavy = false;
                 int32_t e = 0;
                 if (i < n_in) {
+                    ++tl.scanned;
                     e = in ? ld_cg(in + i) : (int32_t)i;
                     alive = ld_cg(a.t + e) == 0;
                     if (alive) {
@@ -352,8 +405,8 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
             if (leader) a.level_of[r + 1] = k;
             const Sinks sk{a.F[fi ^ 1], a.H[fi ^ 1], Wout, &ctl->cntF[pn], &ctl->cntH[pn],
                            &ctl->cntW[wp], baseF[pn], baseH[pn], baseW[wp], thr, bound};
-            process_list<TL>(a, rd, a.F[fi], nF, gwarp, nwarps, sk);
-            process_list<TL>(a, rd, a.H[fi], nH, gwarp, nwarps, sk);
+            process_list<TL>(a, rd, a.F[fi], nF, gwarp, nwarps, sk, tl);
+            process_list<TL>(a, rd, a.H[fi], nH, gwarp, nwarps, sk, tl);
             if (!grid_sync(ctl, &epoch, a.spin_ns, &s_ok)) return;
             const unsigned long long eF = ld_vol(&ctl->cntF[pn]), eH = ld_vol(&ctl->cntH[pn]);
             n_alive -= nF + nH;
@@ -409,6 +462,11 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
         kmax = k;
         ++k;
     }
+    atomicAdd(&ctl->scanned, tl.scanned);
+    atomicAdd(&ctl->entries, tl.entries);
+    atomicAdd(&ctl->searches, tl.searches);
+    atomicAdd(&ctl->lookups, tl.lookups);
+    atomicAdd(&ctl->lowered, tl.lowered);
     if (leader) {
         ctl->kmax = kmax;
         ctl->n_alive = n_alive;
@@ -527,11 +585,22 @@ int run_peel(Graph* g, int32_t k_first, bool single, int32_t* t, PeelCtl* result
     if (per_sm < 1) return fail(TC_ECUDA, "k_peel cannot be resident");
     const int blocks = num_sms() * std::min(per_sm, 2);
     void* params[] = {&a};
+    KernelTimer timer;
+    TC_TRY(timer.start(s));
     TC_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(PK_THREADS), params, 0, s));
     count_launch();
+    TC_TRY(timer.stop(s));
     TC_CUDA_TRY(cudaMemcpyAsync(result, a.ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, s));
     TC_CUDA_TRY(cudaStreamSynchronize(s));
     g->last_peel_rounds = result->rounds;
+    g->stats.peel_ns = timer.elapsed_ns();
+    // algorithmic bytes: a scanned entry reads its id, state and support
+    // (12 B); a triangle-list entry is an 8-B pair, a neighbour-list entry
+    // an id and an edge id (8 B); binary-search steps and state lookups read
+    // 4 B each; a decrement is a 4-B read-modify-write (8 B)
+    g->stats.peel_bytes = 12 * (int64_t)result->scanned + 8 * (int64_t)result->entries +
+                          4 * (int64_t)result->searches + 4 * (int64_t)result->lookups +
+                          8 * (int64_t)result->lowered;
     if (result->abort) return fail(TC_ETIMEDOUT, "peel: a grid barrier wait ran out of time");
     if (result->overflow) return fail(TC_EOVERFLOW, "peel: round table exhausted");
     if (!single) {

@@ -296,9 +296,8 @@ int tc_edges(const tc_graph* g, int32_t* lo, int32_t* hi, void* cuda_stream) {
 int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream) {
     if (!g || !info) return fail(TC_EINVAL, "graph or info is NULL");
     tc::Graph* gg = const_cast<tc::Graph*>(&g->g);
-    DeviceGuard dg(gg->device);
-    int64_t ww = 0;
-    TC_TRY(tc::graph_wedge_work(gg, &ww, as_stream(cuda_stream)));
+    (void)cuda_stream;
+    const int64_t ww = gg->wedge_work;
     info->n = gg->n;
     info->m_in = gg->m_in;
     info->m = gg->m;
@@ -310,7 +309,19 @@ int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream) {
                          (gg->support ? 4 * m : 0);
     info->peel_rounds = gg->last_peel_rounds;
     info->peel_lists = gg->last_peel_lists ? 1 : 0;
+    info->count_kernel_ns = gg->stats.count_ns;
+    info->support_kernel_ns = gg->stats.support_ns;
+    info->lists_kernel_ns = gg->stats.lists_ns;
+    info->peel_kernel_ns = gg->stats.peel_ns;
+    info->peel_bytes = gg->stats.peel_bytes;
     return TC_OK;
+}
+
+int tc_graph_wedge_work(tc_graph* g, int64_t* out, void* cuda_stream) {
+    TC_TRY(begin_call(g, cuda_stream));
+    if (!out) return fail(TC_EINVAL, "out is NULL");
+    DeviceGuard dg(g->g.device);
+    return tc::graph_wedge_work(&g->g, out, as_stream(cuda_stream));
 }
 
 int64_t tc_launch_count(void) { return tc::g_launches.load(); }

@@ -168,6 +168,32 @@ inline int bits_for(uint64_t maxval) {  // bits needed to hold values 0..maxval 
     return b;
 }
 
+// Times one kernel launch with CUDA events on the launching stream.
+struct KernelTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    int start(cudaStream_t s) {
+        TC_CUDA_TRY(cudaEventCreate(&a));
+        TC_CUDA_TRY(cudaEventCreate(&b));
+        TC_CUDA_TRY(cudaEventRecord(a, s));
+        return TC_OK;
+    }
+    int stop(cudaStream_t s) {
+        TC_CUDA_TRY(cudaEventRecord(b, s));
+        return TC_OK;
+    }
+    // valid once the stream has passed the stop event
+    int64_t elapsed_ns() {
+        float ms = 0.f;
+        if (a && b && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) return (int64_t)(ms * 1e6);
+        cudaGetLastError();
+        return -1;
+    }
+    ~KernelTimer() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
 // ---------------------------------------------------------------- primitives
 
 // LSD radix sort of uint64 keys on bits [0, key_bits), stable, optionally
@@ -208,6 +234,10 @@ struct Graph {
     int64_t wedge_work = -1;  // sum of |N+(u)| + |N+(v)| over oriented edges (lazy)
     int64_t last_peel_rounds = 0;  // bulk rounds of the most recent peel
     bool last_peel_lists = false;  // whether it used triangle lists
+    struct {
+        int64_t count_ns = -1, support_ns = -1, lists_ns = -1, peel_ns = -1;
+        int64_t peel_bytes = -1;
+    } stats;  // device time of the latest launch of each main kernel
     // cached support (edge-id order) and triangle count
     int32_t* support = nullptr;
     bool support_valid = false;
