@@ -108,6 +108,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ ranks
+
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The largest value over all ranks (a one-scalar all-reduce; replicas
+    exchange nothing else)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(m_per_rank: int, steps: int, world: int, max_total_ms: float) -> float:
+    """Whole-job edges/s: every rank's replica processes m edges per step; the
+    job takes as long as its slowest rank."""
+    return world * m_per_rank * steps / (max_total_ms / 1e3)
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_step(tc, torch, src, dst, n, wl, stream, ev=None, outs=None, infos=None):
@@ -181,6 +200,84 @@ def kernel_rooflines(infos, count_bytes, support_bytes, lists_bytes, peak):
     return out
 
 
+def bench_batch(args, rank, world):
+    """10,000 independent graphs (n log-uniform in [64, 65536], half
+    Erdős–Rényi with average degree 8-32, half R-MAT edgefactor 16, seed 3):
+    per-graph triangle counts and 4-truss sizes in one tc_batch_run (query
+    phase captured into one CUDA graph), against the same calls made graph by
+    graph on a sample of the batch."""
+    import torch
+    import paper_1708_06866_gb300 as tc
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    n, off, src_h, dst_h, kind = graphgen.batch(args.batch_graphs, seed=3)
+    G = len(n)
+    stream = torch.cuda.Stream()
+    src = torch.from_numpy(src_h).cuda()
+    dst = torch.from_numpy(dst_h).cuda()
+    flush = torch.empty(args.flush_mb << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ref = tc.tc_batch_run(n, off, src, dst, k=4, use_graph=True, stream=stream)
+    torch.cuda.synchronize()
+    step_ms, stats = [], []
+    launches0 = tc.tc_launch_count()
+    sampler = ClockSampler(local)
+    with sampler, torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = tc.tc_batch_run(n, off, src, dst, k=4, use_graph=True, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            stats.append(out["stats"])
+            assert np.array_equal(out["triangles"], ref["triangles"])
+    launches = tc.tc_launch_count() - launches0
+    total_ms = max_over_ranks(float(sum(step_ms)))
+    m_all = int(out["edges"].sum())
+    # the same work graph by graph, on a sample (every graph of the sample
+    # must give the batch's results)
+    rng = np.random.default_rng(5)
+    sample = np.sort(rng.choice(G, min(args.batch_sample, G), replace=False))
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in sample:
+            s = src[off[i]:off[i + 1]]
+            d = dst[off[i]:off[i + 1]]
+            g = tc.tc_build_csr(s, d, int(n[i]), stream=stream)
+            sup, T = tc.tc_edge_support(g, stream=stream)
+            _, left = tc.ktruss(g, 4, stream=stream)
+            assert T == out["triangles"][i] and left == out["truss_edges"][i]
+            g.free()
+        torch.cuda.synchronize()
+        loop_s = time.perf_counter() - t0
+    graphs_per_s = G / (total_ms / args.steps / 1e3)
+    loop_graphs_per_s = len(sample) / loop_s
+    return {"metric": METRIC, "value": world * m_all * args.steps / (total_ms / 1e3),
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "batch10k", "graphs": G, "vertices": int(n.sum()),
+                       "pairs_in": int(off[-1]), "m": m_all,
+                       "triangles": int(out["triangles"].sum()), "k": 4,
+                       "graphs_per_s": graphs_per_s,
+                       "per_graph_loop_graphs_per_s": loop_graphs_per_s,
+                       "per_graph_loop_sample": len(sample),
+                       "speedup_vs_loop": graphs_per_s / loop_graphs_per_s,
+                       "build_ms": float(np.mean([s_["build_ns"] for s_ in stats])) / 1e6,
+                       "query_ms": float(np.mean([s_["query_ns"] for s_ in stats])) / 1e6,
+                       "tuner": {k_: stats[-1][k_] for k_ in ("intersect_form", "peel_form",
+                                                              "tuned_from_cache", "captured")},
+                       "l2": f"flushed between steps ({args.flush_mb} MB write)",
+                       "parallelism": "single"},
+            "gpu_launches": launches, "clocks": sampler.summary()}
+
+
 def bench_ours(args, rank, world):
     import torch
     import paper_1708_06866_gb300 as tc
@@ -238,13 +335,9 @@ def bench_ours(args, rank, world):
                 for (a, ea), (b, eb) in zip(ev[:-1], ev[1:]):
                     phases.setdefault(b, []).append(ea.elapsed_time(eb))
     launches = tc.tc_launch_count() - launches0
-    total_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(step_ms)), dist, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * m * args.steps / (total_ms / 1e3)
+    value = job_rate(m, args.steps, world, total_ms)
 
     # roofline of the dominant kernel: the library times each launch of its
     # main kernels with CUDA events on the call's stream, in every timed step
@@ -383,7 +476,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(graphgen.WORKLOADS), default="rmat20")
+    ap.add_argument("--workload", choices=sorted(graphgen.WORKLOADS) + ["batch10k"],
+                    default="rmat20")
+    ap.add_argument("--batch-graphs", type=int, default=10_000)
+    ap.add_argument("--batch-sample", type=int, default=300)
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -392,6 +488,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         out = bench_reference(args, rank, world)
+    elif args.workload == "batch10k":
+        out = bench_batch(args, rank, world)
     else:
         out = bench_ours(args, rank, world)
     if rank == 0 and out is not None:

@@ -57,6 +57,10 @@ def _load():
                                       ctypes.c_int, i32p, i32p]
             lib.gg_er.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, i32p, i32p]
             lib.gg_permutation.argtypes = [ctypes.c_int32, ctypes.c_uint64, i32p]
+            vp = ctypes.c_void_p
+            lib.gg_batch.argtypes = [ctypes.c_int32, vp, vp, vp, vp, ctypes.c_uint64,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, i32p, i32p]
+            lib.gg_batch.restype = ctypes.c_int
             for f in (lib.gg_rmat, lib.gg_rmat_n, lib.gg_er):
                 f.restype = ctypes.c_int
             lib.gg_permutation.restype = None
@@ -193,6 +197,35 @@ def messy(src: np.ndarray, dst: np.ndarray, seed: int = 0, loops: int = 0,
     d = np.concatenate(parts_d).astype(np.int32)
     order = rng.permutation(len(s))
     return s[order], d[order]
+
+
+def batch(num_graphs: int = 10_000, seed: int = 3, n_min: int = 64, n_max: int = 65_536,
+          er_degree=(8.0, 32.0), edgefactor: int = 16, a: float = 0.57, b: float = 0.19,
+          c: float = 0.19):
+    """Many independent graphs: n log-uniform in [n_min, n_max]; even-indexed
+    graphs Erdős–Rényi with average degree uniform in er_degree, odd-indexed
+    R-MAT with edgefactor * n draws (endpoints >= n rejected), permuted.
+
+    Returns (n, edge_off, src, dst, kind): per-graph vertex counts, offsets
+    into the concatenated pair lists (ids local to each graph), the kinds.
+    """
+    rng = np.random.default_rng(seed)
+    n = np.exp(rng.uniform(np.log(n_min), np.log(n_max), num_graphs)).round().astype(np.int64)
+    n = np.clip(n, n_min, n_max)
+    kind = (np.arange(num_graphs) % 2).astype(np.int32)
+    deg = rng.uniform(er_degree[0], er_degree[1], num_graphs)
+    m = np.where(kind == 0, np.round(n * deg / 2.0), edgefactor * n).astype(np.int64)
+    m = np.where(kind == 0, np.minimum(m, (n * (n - 1)) // 4), m)   # ER: at most half the pairs
+    off = np.zeros(num_graphs + 1, dtype=np.int64)
+    np.cumsum(m, out=off[1:])
+    src = np.empty(off[-1], dtype=np.int32)
+    dst = np.empty(off[-1], dtype=np.int32)
+    n32 = np.ascontiguousarray(n, dtype=np.int32)
+    rc = _load().gg_batch(num_graphs, kind.ctypes.data, n32.ctypes.data, m.ctypes.data,
+                          off.ctypes.data, seed, a, b, c, _p(src), _p(dst))
+    if rc != 0:
+        raise ValueError("gg_batch failed")
+    return n32, off, src, dst, kind
 
 
 @dataclasses.dataclass(frozen=True)

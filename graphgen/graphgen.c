@@ -193,3 +193,23 @@ int gg_er(int32_t n, int64_t m, uint64_t seed, int32_t* src, int32_t* dst) {
     free(set);
     return 0;
 }
+
+/* A batch of independent graphs, generated in parallel (one graph per task):
+ * kind[g] = 0: Erdős–Rényi G(n[g], m[g]); kind[g] = 1: R-MAT on n[g]
+ * vertices with m[g] draws (rejection of endpoints >= n[g]), permuted.
+ * Graph g's pairs go to src/dst[off[g] .. off[g] + m[g]); its stream seed is
+ * derived from (seed, g). */
+int gg_batch(int32_t G, const int32_t* kind, const int32_t* n, const int64_t* m,
+             const int64_t* off, uint64_t seed, double a, double b, double c, int32_t* src,
+             int32_t* dst) {
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(| : bad)
+    for (int32_t g = 0; g < G; ++g) {
+        const uint64_t sg = mix64(seed * 0x100000001b3ULL + (uint64_t)g + 1);
+        int rc;
+        if (kind[g] == 0) rc = gg_er(n[g], m[g], sg, src + off[g], dst + off[g]);
+        else rc = gg_rmat_n(n[g], m[g], a, b, c, sg, 1, src + off[g], dst + off[g]);
+        if (rc != 0) bad = 1;
+    }
+    return bad ? -1 : 0;
+}

@@ -181,6 +181,50 @@ int tc_graph_wedge_work(tc_graph* g, int64_t* out, void* cuda_stream);
  * graphs, all threads); lets a caller count the launches of a region. */
 int64_t tc_launch_count(void);
 
+/*
+ * Batches: many independent graphs in one pass.
+ *
+ * tc_batch_run cleans and builds all graphs of the batch as one graph (the
+ * disjoint union, vertex ids offset per graph: a triangle or a k-truss never
+ * spans two graphs, so the union's triangles and trusses are exactly the
+ * graphs'), then computes per-graph triangle counts (Section III-A) and,
+ * if k >= 2, per-graph k-truss sizes (Section III-B) with one launch per
+ * phase over all graphs.  With use_graph = 1 the query phase (supports,
+ * per-graph sums, the peel) is captured into one CUDA graph and launched
+ * once.  The first batch with a given size/degree signature times both
+ * masked-product kernels and both peel forms on the batch and keeps the
+ * fastest; later batches with that signature reuse the choice.
+ */
+typedef struct {
+    int64_t build_ns;          /* union build, CUDA events on the call's stream */
+    int64_t query_ns;          /* supports + per-graph sums + peel */
+    int64_t m;                 /* edges of all graphs after cleaning */
+    int64_t triangles;         /* triangles of all graphs */
+    int32_t intersect_form;    /* 1 = row/hash kernel, 2 = edge-per-warp kernel */
+    int32_t peel_form;         /* 0 = no peel, 1 = triangle lists, 2 = intersections */
+    int32_t tuned_from_cache;  /* 1 if the kernel choice came from the tuner's cache */
+    int32_t captured;          /* 1 if the query ran as one CUDA graph launch */
+} tc_batch_stats_t;
+
+typedef struct {
+    int32_t num_graphs;          /* >= 1 */
+    const int32_t* n;            /* host: vertices of each graph (each >= 1; sum < 2^31) */
+    const int64_t* edge_off;     /* host: num_graphs + 1 offsets into src/dst, edge_off[0] = 0 */
+    const int32_t* src;          /* edge_off[num_graphs] pairs, ids local to their graph */
+    const int32_t* dst;          /* (device or host) */
+    int32_t k;                   /* k-truss per graph (>= 2), or 0 for triangle counts only */
+    int32_t use_graph;           /* 1: run the query phase as one captured CUDA graph */
+    int64_t* triangles_out;      /* host: num_graphs triangle counts (required) */
+    int64_t* edges_out;          /* host: num_graphs edge counts after cleaning, or NULL */
+    int64_t* truss_edges_out;    /* host: num_graphs k-truss edge counts, or NULL */
+    tc_batch_stats_t* stats_out; /* host, or NULL */
+} tc_batch_desc;
+
+/* Runs a batch.  Synchronises the stream (NULL: the library uses a private
+ * stream).  Errors: TC_EINVAL (bad descriptor), TC_ERANGE (a local id outside
+ * its graph), TC_EOVERFLOW, TC_ENOMEM, TC_ECUDA, TC_ETIMEDOUT. */
+int tc_batch_run(const tc_batch_desc* d, void* cuda_stream);
+
 /* Releases a graph (NULL is a no-op).  Synchronises the device's work on
  * the graph's last stream first. */
 void tc_graph_free(tc_graph* g);

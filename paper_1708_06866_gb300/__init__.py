@@ -29,7 +29,7 @@ from . import _build
 __all__ = [
     "TCError", "Graph", "load_library", "library_path", "tc_build_csr", "tc_count",
     "tc_edge_support", "ktruss", "ktruss_max", "tc_num_edges", "tc_num_vertices", "tc_edges",
-    "tc_graph_info", "tc_graph_wedge_work", "tc_launch_count",
+    "tc_graph_info", "tc_graph_wedge_work", "tc_launch_count", "tc_batch_run",
     "tc_graph_free", "tc_strerror", "tc_last_error", "tc_debug_fail_alloc",
     "tc_debug_spin_limit_ns", "tc_debug_peel_mode", "tc_debug_intersect_mode", "TC_OK", "TC_EINVAL", "TC_ERANGE", "TC_ENOMEM", "TC_ECUDA",
     "TC_ETIMEDOUT", "TC_EOVERFLOW", "TC_INPUT_AUTO", "TC_INPUT_DEVICE", "TC_INPUT_HOST",
@@ -73,6 +73,7 @@ def load_library(build_if_missing: bool = True):
             "tc_last_error": (ctypes.c_char_p, []),
             "tc_graph_info": (ctypes.c_int, [vp, ctypes.POINTER(GraphInfo), vp]),
             "tc_launch_count": (i64, []),
+            "tc_batch_run": (ctypes.c_int, [ctypes.POINTER(BatchDesc), vp]),
             "tc_graph_wedge_work": (ctypes.c_int, [vp, ctypes.POINTER(i64), vp]),
             "tc_debug_fail_alloc": (i64, [i64]),
             "tc_debug_spin_limit_ns": (i64, [i64]),
@@ -96,6 +97,26 @@ class GraphInfo(ctypes.Structure):
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class BatchStats(ctypes.Structure):
+    """Mirror of tc_batch_stats_t."""
+    _fields_ = [("build_ns", ctypes.c_int64), ("query_ns", ctypes.c_int64),
+                ("m", ctypes.c_int64), ("triangles", ctypes.c_int64),
+                ("intersect_form", ctypes.c_int32), ("peel_form", ctypes.c_int32),
+                ("tuned_from_cache", ctypes.c_int32), ("captured", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class BatchDesc(ctypes.Structure):
+    """Mirror of tc_batch_desc."""
+    _fields_ = [("num_graphs", ctypes.c_int32), ("n", ctypes.c_void_p),
+                ("edge_off", ctypes.c_void_p), ("src", ctypes.c_void_p),
+                ("dst", ctypes.c_void_p), ("k", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("triangles_out", ctypes.c_void_p), ("edges_out", ctypes.c_void_p),
+                ("truss_edges_out", ctypes.c_void_p), ("stats_out", ctypes.c_void_p)]
 
 
 class TCError(RuntimeError):
@@ -295,6 +316,31 @@ def tc_graph_wedge_work(g: Graph, stream=None) -> int:
 def tc_launch_count() -> int:
     """Kernels launched by the library so far in this process."""
     return int(load_library().tc_launch_count())
+
+
+def tc_batch_run(n, edge_off, src, dst, k: int = 0, use_graph: bool = True, stream=None):
+    """Triangle counts (and k-truss sizes if k >= 2) of many graphs in one pass.
+
+    n: vertices per graph; edge_off: num_graphs + 1 offsets into the
+    concatenated src/dst (ids local to each graph).  Returns a dict with
+    numpy arrays "triangles", "edges", "truss_edges" and "stats".
+    """
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    edge_off = np.ascontiguousarray(edge_off, dtype=np.int64)
+    G = len(n)
+    if len(edge_off) != G + 1:
+        raise ValueError("edge_off must have num_graphs + 1 entries")
+    src = _as_int32(src)
+    dst = _as_int32(dst)
+    tri = np.zeros(G, dtype=np.int64)
+    edges = np.zeros(G, dtype=np.int64)
+    truss = np.zeros(G, dtype=np.int64)
+    stats = BatchStats()
+    d = BatchDesc(G, n.ctypes.data, edge_off.ctypes.data, _ptr(src), _ptr(dst), int(k),
+                  int(bool(use_graph)), tri.ctypes.data, edges.ctypes.data, truss.ctypes.data,
+                  ctypes.addressof(stats))
+    _check(load_library().tc_batch_run(ctypes.byref(d), _stream_handle(stream)), "tc_batch_run")
+    return {"triangles": tri, "edges": edges, "truss_edges": truss, "stats": stats.as_dict()}
 
 
 def tc_graph_free(g: Graph):

@@ -392,13 +392,14 @@ int graph_wedge_work(Graph* g, int64_t* out, cudaStream_t s) {
 }
 
 int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangles,
-                    cudaStream_t s) {
+                    cudaStream_t s, int form) {
     const int64_t m = g->m;
     if (m == 0) {
         if (triangles) *triangles = 0;
         return TC_OK;
     }
-    const bool rows = g->max_out <= RX_MAX_OUT && intersect_mode() != 2;
+    const int f = form != 0 ? form : intersect_mode();
+    const bool rows = g->max_out <= RX_MAX_OUT && f != 2;
     const int blocks = rows ? rows_blocks(g, want_support ? SUPPORT : COUNT) : num_sms() * 8;
     Scratch sc(s);
     unsigned long long* partials;
@@ -434,41 +435,35 @@ int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangle
 
 bool triangle_lists_supported(const Graph* g) { return g->max_out <= RX_MAX_OUT; }
 
-int exclusive_scan_i32(const int32_t* x, int64_t n, unsigned long long* off, cudaStream_t s) {
-    const int64_t chunks = (n + SC_CHUNK - 1) / SC_CHUNK;
-    Scratch sc(s);
-    unsigned long long* sums;
-    TC_TRY(sc.alloc(&sums, chunks));
-    k_chunk_sums<<<(unsigned)chunks, SC_THREADS, 0, s>>>(x, n, sums);
-    TC_LAUNCH_CHECK("k_chunk_sums");
-    k_scan_sums64<<<1, 1024, 0, s>>>(sums, chunks);
-    TC_LAUNCH_CHECK("k_scan_sums64");
-    k_chunk_scan<<<(unsigned)chunks, SC_THREADS, 0, s>>>(x, n, sums, off);
-    TC_LAUNCH_CHECK("k_chunk_scan");
+int plan_triangle_lists(Graph* g, Scratch& sc, ListsPlan* lp) {
+    const int64_t m = g->m;
+    lp->chunks = (m + SC_CHUNK - 1) / SC_CHUNK;
+    TC_TRY(sc.alloc(&lp->sums, lp->chunks));
+    TC_TRY(sc.alloc(&lp->cursor, m));
+    lp->blocks = rows_blocks(g, LISTS);
+    TC_TRY(sc.alloc(&lp->partials, lp->blocks));
     return TC_OK;
 }
 
-int build_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off, int2* pairs,
-                         cudaStream_t s) {
+// Offsets = exclusive scan of the supports; then every triangle writes its
+// pair into the lists of its three edges.  List positions fit in 32 bits
+// (the caller keeps 3T below 2^32), so a 4-byte cursor per edge keeps the
+// cursor array small enough for L2.
+int enqueue_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off, int2* pairs,
+                           ListsPlan* lp, cudaStream_t s) {
     const int64_t m = g->m;
-    TC_TRY(exclusive_scan_i32(sup, m, off, s));
-    Scratch sc(s);
-    // list positions fit in 32 bits (the caller keeps 3T below 2^32): a
-    // 4-byte cursor per edge keeps the cursor array small enough for L2
-    unsigned int* cursor;
-    TC_TRY(sc.alloc(&cursor, m));
+    k_chunk_sums<<<(unsigned)lp->chunks, SC_THREADS, 0, s>>>(sup, m, lp->sums);
+    TC_LAUNCH_CHECK("k_chunk_sums");
+    k_scan_sums64<<<1, 1024, 0, s>>>(lp->sums, lp->chunks);
+    TC_LAUNCH_CHECK("k_scan_sums64");
+    k_chunk_scan<<<(unsigned)lp->chunks, SC_THREADS, 0, s>>>(sup, m, lp->sums, off);
+    TC_LAUNCH_CHECK("k_chunk_scan");
     k_u32_from_u64<<<(unsigned)std::min<int64_t>((m + 255) / 256, (int64_t)num_sms() * 16), 256, 0,
-                     s>>>(off, m, cursor);
+                     s>>>(off, m, lp->cursor);
     TC_LAUNCH_CHECK("k_u32_from_u64");
-    const int blocks = rows_blocks(g, LISTS);
-    unsigned long long* partials;
-    TC_TRY(sc.alloc(&partials, blocks));
-    KernelTimer timer;
-    TC_TRY(timer.start(s));
-    TC_TRY(launch_rows<LISTS>(g, nullptr, cursor, pairs, partials, blocks, s));
-    TC_TRY(timer.stop(s));
-    TC_CUDA_TRY(cudaStreamSynchronize(s));
-    g->stats.lists_ns = timer.elapsed_ns();
+    TC_TRY(lp->timer.start(s));
+    TC_TRY(launch_rows<LISTS>(g, nullptr, lp->cursor, pairs, lp->partials, lp->blocks, s));
+    TC_TRY(lp->timer.stop(s));
     return TC_OK;
 }
 

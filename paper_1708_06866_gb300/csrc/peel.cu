@@ -24,6 +24,7 @@
 // Edge state t[e]: 0 = alive, -1 = in the current frontier, > 0 = removed.
 #include <algorithm>
 #include <climits>
+#include <new>
 
 #include "tc_internal.cuh"
 
@@ -501,7 +502,7 @@ __global__ void k_truss_from_state(int32_t* __restrict__ t, int64_t m,
     }
 }
 
-int ensure_support(Graph* g, cudaStream_t s) {
+int ensure_support_impl(Graph* g, cudaStream_t s) {
     if (g->support_valid) return TC_OK;
     if (!g->support) TC_TRY(dev_alloc_n(&g->support, g->m, s));
     int64_t T = 0;
@@ -516,15 +517,39 @@ inline unsigned small_grid(int64_t items) {
                                                             (items + 255) / 256));
 }
 
-// Runs the persistent peel.  t (m entries, device) receives the edge states.
-// The triangle-list form is used when the lists (3T pairs of edge ids) fit
-// comfortably in free device memory, unless a test hook forces a form.
-int run_peel(Graph* g, int32_t k_first, bool single, int32_t* t, PeelCtl* result,
-             cudaStream_t s) {
-    const int64_t m = g->m;
-    TC_TRY(ensure_support(g, s));
-    Scratch sc(s);
+}  // namespace
+
+// A peel split into host planning (decisions and every allocation), stream
+// work (capturable in a CUDA graph: no host synchronisation) and completion
+// (reads the control block back).  The triangle-list form is used when the
+// lists (3T pairs of edge ids) fit comfortably in free device memory, unless
+// the caller or a test hook forces a form.
+struct PeelPlan {
+    Graph* g = nullptr;
     PeelArgs a{};
+    bool tl = false;
+    bool single = false;
+    const void* fn = nullptr;
+    int blocks = 0;
+    unsigned long long* off = nullptr;
+    int2* pairs = nullptr;
+    ListsPlan lists;
+    KernelTimer timer;
+    PeelCtl result{};
+};
+
+PeelPlan* peel_plan_new() { return new (std::nothrow) PeelPlan(); }
+void peel_plan_delete(PeelPlan* p) { delete p; }
+
+int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single, int32_t* t,
+              int form) {
+    PeelPlan& p = *pp;
+    const int64_t m = g->m;
+    if (!g->support_valid) return fail(TC_EINVAL, "internal: peel planned without supports");
+    p.g = g;
+    p.single = single;
+    PeelArgs& a = p.a;
+    a = PeelArgs{};
     a.m = m;
     a.n = g->n;
     a.ends = g->ends;
@@ -533,36 +558,26 @@ int run_peel(Graph* g, int32_t k_first, bool single, int32_t* t, PeelCtl* result
     a.k_first = k_first;
     a.single = single ? 1 : 0;
     a.spin_ns = spin_limit_ns();
-
-    const int forced = peel_mode();
-    bool tl = false;
+    const int forced = form != PEEL_AUTO ? form : peel_mode();
+    p.tl = false;
     // list positions are 32-bit: the triangle-list form needs 3T < 2^32
     if (triangle_lists_supported(g) && forced != PEEL_INTERSECT &&
         3 * g->triangles < 0xffffffffLL) {
         const double need = 24.0 * (double)g->triangles + 16.0 * (double)(m + 1);
         size_t free_b = 0, total_b = 0;
         TC_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-        tl = forced == PEEL_LISTS || need < 0.6 * (double)free_b;
+        p.tl = forced == PEEL_LISTS || need < 0.6 * (double)free_b;
     }
-    g->last_peel_lists = tl;
-    if (tl) {
-        unsigned long long* off;
-        int2* pairs;
-        TC_TRY(sc.alloc(&off, m + 1));
-        TC_TRY(sc.alloc(&pairs, std::max<int64_t>(1, 3 * g->triangles)));
-        TC_TRY(build_triangle_lists(g, g->support, off, pairs, s));
-        a.off = off;
-        a.pairs = pairs;
+    if (p.tl) {
+        TC_TRY(sc.alloc(&p.off, m + 1));
+        TC_TRY(sc.alloc(&p.pairs, std::max<int64_t>(1, 3 * g->triangles)));
+        TC_TRY(plan_triangle_lists(g, sc, &p.lists));
+        a.off = p.off;
+        a.pairs = p.pairs;
     } else {
         TC_TRY(sc.alloc(&a.rowlen, g->n));
         TC_TRY(sc.alloc(&a.col, 2 * m));
         TC_TRY(sc.alloc(&a.eid, 2 * m));
-        TC_CUDA_TRY(cudaMemcpyAsync(a.col, g->col, sizeof(int32_t) * 2 * m,
-                                    cudaMemcpyDeviceToDevice, s));
-        TC_CUDA_TRY(cudaMemcpyAsync(a.eid, g->eid, sizeof(int32_t) * 2 * m,
-                                    cudaMemcpyDeviceToDevice, s));
-        k_peel_init<<<small_grid(g->n), 256, 0, s>>>(g->rowptr, g->n, a.rowlen);
-        TC_LAUNCH_CHECK("k_peel_init");
     }
     TC_TRY(sc.alloc(&a.s, m));
     for (int i = 0; i < 2; ++i) {
@@ -572,45 +587,102 @@ int run_peel(Graph* g, int32_t k_first, bool single, int32_t* t, PeelCtl* result
         TC_TRY(sc.alloc(&a.H[i], m));
     }
     TC_TRY(sc.alloc(&a.ctl, 1));
-    a.max_round = 2 * m + 16;
-    if (a.max_round > 0x7fffffffLL) return fail(TC_EOVERFLOW, "peel: more than 2^30 edges");
+    // round numbers live in int32 edge states: at most 2^31 - 16 rounds (a
+    // round removes at least one edge, so m + levels bounds them; the kernel
+    // stops with an overflow status if the table ever runs out)
+    a.max_round = std::min<int64_t>(2 * m + 16, 0x7fffffffLL - 16);
     TC_TRY(sc.alloc(&a.level_of, a.max_round));
-    TC_CUDA_TRY(cudaMemcpyAsync(a.s, g->support, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
-    TC_CUDA_TRY(cudaMemsetAsync(t, 0, sizeof(int32_t) * m, s));
-    TC_CUDA_TRY(cudaMemsetAsync(a.ctl, 0, sizeof(PeelCtl), s));
-
-    const void* fn = tl ? (const void*)k_peel<true> : (const void*)k_peel<false>;
+    p.fn = p.tl ? (const void*)k_peel<true> : (const void*)k_peel<false>;
     int per_sm = 0;
-    TC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PK_THREADS, 0));
+    TC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p.fn, PK_THREADS, 0));
     if (per_sm < 1) return fail(TC_ECUDA, "k_peel cannot be resident");
-    const int blocks = num_sms() * std::min(per_sm, 2);
+    // small graphs get a smaller grid (cheaper barriers, and room for other
+    // streams' work); large ones fill every SM twice
+    const int64_t want = std::max<int64_t>(1, (m + 8191) / 8192);
+    p.blocks = (int)std::min<int64_t>(want, (int64_t)num_sms() * std::min(per_sm, 2));
+    g->last_peel_lists = p.tl;
+    return TC_OK;
+}
+
+int peel_enqueue(PeelPlan* pp, cudaStream_t s) {
+    PeelPlan& p = *pp;
+    Graph* g = p.g;
+    PeelArgs& a = p.a;
+    const int64_t m = g->m;
+    if (p.tl) {
+        TC_TRY(enqueue_triangle_lists(g, g->support, p.off, p.pairs, &p.lists, s));
+    } else {
+        TC_CUDA_TRY(cudaMemcpyAsync(a.col, g->col, sizeof(int32_t) * 2 * m,
+                                    cudaMemcpyDeviceToDevice, s));
+        TC_CUDA_TRY(cudaMemcpyAsync(a.eid, g->eid, sizeof(int32_t) * 2 * m,
+                                    cudaMemcpyDeviceToDevice, s));
+        k_peel_init<<<small_grid(g->n), 256, 0, s>>>(g->rowptr, g->n, a.rowlen);
+        TC_LAUNCH_CHECK("k_peel_init");
+    }
+    TC_CUDA_TRY(cudaMemcpyAsync(a.s, g->support, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
+    TC_CUDA_TRY(cudaMemsetAsync(a.t, 0, sizeof(int32_t) * m, s));
+    TC_CUDA_TRY(cudaMemsetAsync(a.ctl, 0, sizeof(PeelCtl), s));
     void* params[] = {&a};
-    KernelTimer timer;
-    TC_TRY(timer.start(s));
-    TC_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(PK_THREADS), params, 0, s));
+    TC_TRY(p.timer.start(s));
+    TC_CUDA_TRY(cudaLaunchCooperativeKernel(p.fn, dim3(p.blocks), dim3(PK_THREADS), params, 0, s));
     count_launch();
-    TC_TRY(timer.stop(s));
-    TC_CUDA_TRY(cudaMemcpyAsync(result, a.ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, s));
-    TC_CUDA_TRY(cudaStreamSynchronize(s));
-    g->last_peel_rounds = result->rounds;
-    g->stats.peel_ns = timer.elapsed_ns();
-    // algorithmic bytes: a scanned entry reads its id, state and support
-    // (12 B); a triangle-list entry is an 8-B pair, a neighbour-list entry
-    // an id and an edge id (8 B); binary-search steps and state lookups read
-    // 4 B each; a decrement is a 4-B read-modify-write (8 B)
-    g->stats.peel_bytes = 12 * (int64_t)result->scanned + 8 * (int64_t)result->entries +
-                          4 * (int64_t)result->searches + 4 * (int64_t)result->lookups +
-                          8 * (int64_t)result->lowered;
-    if (result->abort) return fail(TC_ETIMEDOUT, "peel: a grid barrier wait ran out of time");
-    if (result->overflow) return fail(TC_EOVERFLOW, "peel: round table exhausted");
-    if (!single) {
-        k_truss_from_state<<<small_grid(m), 256, 0, s>>>(t, m, a.level_of);
+    TC_TRY(p.timer.stop(s));
+    if (!p.single) {
+        k_truss_from_state<<<small_grid(m), 256, 0, s>>>(a.t, m, a.level_of);
         TC_LAUNCH_CHECK("k_truss_from_state");
     }
     return TC_OK;
 }
 
+int peel_finish(PeelPlan* pp, cudaStream_t s, int64_t* n_alive, int32_t* kmax) {
+    PeelPlan& p = *pp;
+    Graph* g = p.g;
+    PeelCtl& r = p.result;
+    TC_CUDA_TRY(cudaMemcpyAsync(&r, p.a.ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, s));
+    TC_CUDA_TRY(cudaStreamSynchronize(s));
+    g->last_peel_rounds = r.rounds;
+    g->stats.peel_ns = p.timer.elapsed_ns();
+    if (p.tl) g->stats.lists_ns = p.lists.timer.elapsed_ns();
+    // algorithmic bytes: a scanned entry reads its id, state and support
+    // (12 B); a triangle-list entry is an 8-B pair, a neighbour-list entry
+    // an id and an edge id (8 B); binary-search steps and state lookups read
+    // 4 B each; a decrement is a 4-B read-modify-write (8 B)
+    g->stats.peel_bytes = 12 * (int64_t)r.scanned + 8 * (int64_t)r.entries +
+                          4 * (int64_t)r.searches + 4 * (int64_t)r.lookups +
+                          8 * (int64_t)r.lowered;
+    if (r.abort) return fail(TC_ETIMEDOUT, "peel: a grid barrier wait ran out of time");
+    if (r.overflow) return fail(TC_EOVERFLOW, "peel: round table exhausted");
+    if (n_alive) *n_alive = r.n_alive;
+    if (kmax) *kmax = r.kmax;
+    return TC_OK;
+}
+
+bool peel_uses_lists(const PeelPlan* p) { return p->tl; }
+
+namespace {
+
+// Plan, run and complete one peel on the graph's stream.
+int run_peel(Graph* g, int32_t k_first, bool single, int32_t* t, PeelCtl* result,
+             cudaStream_t s) {
+    TC_TRY(ensure_support_impl(g, s));
+    Scratch sc(s);
+    PeelPlan p;
+    TC_TRY(peel_plan(&p, sc, g, k_first, single, t, PEEL_AUTO));
+    TC_TRY(peel_enqueue(&p, s));
+    TC_TRY(peel_finish(&p, s, nullptr, nullptr));
+    *result = p.result;
+    return TC_OK;
+}
+
 }  // namespace
+
+int ensure_support(Graph* g, cudaStream_t s) { return ensure_support_impl(g, s); }
+
+int mask_from_state(const int32_t* t, int64_t m, uint8_t* mask, cudaStream_t s) {
+    k_mask_from_state<<<small_grid(m), 256, 0, s>>>(t, m, mask);
+    TC_LAUNCH_CHECK("k_mask_from_state");
+    return TC_OK;
+}
 
 int peel_ktruss(Graph* g, int32_t k, uint8_t* mask, int64_t* edges_left, cudaStream_t s) {
     const int64_t m = g->m;
@@ -623,8 +695,7 @@ int peel_ktruss(Graph* g, int32_t k, uint8_t* mask, int64_t* edges_left, cudaStr
     TC_TRY(sc.alloc(&t, m));
     PeelCtl r{};
     TC_TRY(run_peel(g, k, true, t, &r, s));
-    k_mask_from_state<<<small_grid(m), 256, 0, s>>>(t, m, mask);
-    TC_LAUNCH_CHECK("k_mask_from_state");
+    TC_TRY(mask_from_state(t, m, mask, s));
     if (edges_left) *edges_left = r.n_alive;
     return TC_OK;
 }

@@ -247,10 +247,38 @@ struct Graph {
     cudaStream_t last_stream = nullptr;
 };
 
+// Scratch of a triangle-list build (planned before, enqueued later).
+struct ListsPlan {
+    unsigned long long* sums = nullptr;  // per-chunk sums of the offset scan
+    int64_t chunks = 0;
+    unsigned int* cursor = nullptr;      // per-edge fill positions
+    unsigned long long* partials = nullptr;
+    int blocks = 0;
+    KernelTimer timer;
+};
+int plan_triangle_lists(Graph* g, Scratch& sc, ListsPlan* lp);
+int enqueue_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off, int2* pairs,
+                           ListsPlan* lp, cudaStream_t s);
+
+// Peel: plan (host decisions and allocations), enqueue (stream work only,
+// capturable), finish (reads results back; synchronises).
+struct PeelPlan;
+PeelPlan* peel_plan_new();
+void peel_plan_delete(PeelPlan* p);
+int peel_plan(PeelPlan* p, Scratch& sc, Graph* g, int32_t k_first, bool single, int32_t* t,
+              int form);
+int peel_enqueue(PeelPlan* p, cudaStream_t s);
+int peel_finish(PeelPlan* p, cudaStream_t s, int64_t* n_alive, int32_t* kmax);
+bool peel_uses_lists(const PeelPlan* p);
+int ensure_support(Graph* g, cudaStream_t s);
+int mask_from_state(const int32_t* t, int64_t m, uint8_t* mask, cudaStream_t s);
+
 int build_graph(Graph* g, const int32_t* src_d, const int32_t* dst_d, cudaStream_t s);
 void free_graph(Graph* g);
+// form: 0 = automatic (honours the test hook), 1 = row/hash kernel where the
+// graph allows it, 2 = edge-per-warp kernel.
 int compute_support(Graph* g, int32_t* s_out_dev, bool want_support, int64_t* triangles,
-                    cudaStream_t s);
+                    cudaStream_t s, int form = 0);
 int peel_ktruss(Graph* g, int32_t k, uint8_t* mask_dev, int64_t* edges_left, cudaStream_t s);
 int graph_wedge_work(Graph* g, int64_t* out, cudaStream_t s);
 bool triangle_lists_supported(const Graph* g);

@@ -1,0 +1,59 @@
+"""Host-side logic of bench.py, on CPU: the replicas' max-over-ranks timing
+with two gloo ranks, the whole-job rate, and the reference arm's rank rule."""
+import os
+import socket
+import sys
+
+import pytest
+
+from conftest import ROOT
+
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, values, out):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        got = bench.max_over_ranks(values[rank], dist, "cpu")
+        out.put((rank, got))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_two_gloo_ranks():
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    values = [12.5, 40.25]
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, values, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res == {0: 40.25, 1: 40.25}
+
+
+def test_job_rate_counts_all_ranks():
+    assert bench.max_over_ranks(7.0) == 7.0
+    # 2 ranks x 1e6 edges x 4 steps in 2 s
+    assert bench.job_rate(1_000_000, 4, 2, 2000.0) == pytest.approx(4e6)
+
+
+def test_reference_arm_only_rank0_reports(monkeypatch):
+    class A:
+        steps, warmup, workload = 1, 0, "rmat20"
+    assert bench.bench_reference(A(), rank=1, world=2) is None
