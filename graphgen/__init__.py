@@ -228,6 +228,31 @@ def batch(num_graphs: int = 10_000, seed: int = 3, n_min: int = 64, n_max: int =
     return n32, off, src, dst, kind
 
 
+def rmat_pool(num_graphs: int = 64, seed: int = 4, n_min: int = 1 << 10, n_max: int = 1 << 22,
+              edgefactor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19):
+    """A pool of R-MAT graphs for serving: n log-uniform in [n_min, n_max],
+    edgefactor * n draws each (endpoints >= n rejected), permuted.
+
+    Returns {graph id: (src, dst, n)} (views into two concatenated arrays).
+    """
+    rng = np.random.default_rng(seed)
+    n = np.exp(rng.uniform(np.log(n_min), np.log(n_max), num_graphs)).round().astype(np.int64)
+    n = np.clip(n, n_min, n_max)
+    m = edgefactor * n
+    off = np.zeros(num_graphs + 1, dtype=np.int64)
+    np.cumsum(m, out=off[1:])
+    src = np.empty(off[-1], dtype=np.int32)
+    dst = np.empty(off[-1], dtype=np.int32)
+    kind = np.ones(num_graphs, dtype=np.int32)
+    n32 = np.ascontiguousarray(n, dtype=np.int32)
+    rc = _load().gg_batch(num_graphs, kind.ctypes.data, n32.ctypes.data, m.ctypes.data,
+                          off.ctypes.data, seed, a, b, c, _p(src), _p(dst))
+    if rc != 0:
+        raise ValueError("gg_batch failed")
+    return {g: (src[off[g]:off[g + 1]], dst[off[g]:off[g + 1]], int(n[g]))
+            for g in range(num_graphs)}
+
+
 @dataclasses.dataclass(frozen=True)
 class Workload:
     """A named synthetic workload: generator family, sizes and seed."""

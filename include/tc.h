@@ -108,6 +108,9 @@ int tc_edge_support(tc_graph* g, int32_t* support_out, int64_t* triangles_out,
  * support is below k - 2 are removed in bulk rounds and the supports of the
  * edges sharing their triangles are lowered, until no edge is below
  * (Algorithm 4's loop).  k >= 2 (k = 2 keeps every edge).
+ * The graph keeps the supports, and the per-edge triangle lists when the
+ * peel builds them and they fit, for later ktruss / ktruss_max calls
+ * (tc_graph_info's device_bytes counts them).
  * mask_out: m uint8 in edge-id order, 1 = in the k-truss (device or host).
  * edges_out: host int64, number of edges in the k-truss; may be NULL.
  * Errors: TC_EINVAL for k < 2.
@@ -150,7 +153,8 @@ typedef struct {
     int64_t wedge_work;    /* sum over oriented edges (u, v) of |N+(u)| + |N+(v)|
                               (the list entries a merge-based masked product
                               reads), or -1 until tc_graph_wedge_work ran */
-    int64_t device_bytes;  /* device memory held by the graph */
+    int64_t device_bytes;  /* device memory held by the graph (CSR, edge arrays,
+                              cached supports and cached triangle lists) */
     int64_t peel_rounds;   /* bulk removal rounds of the most recent ktruss /
                               ktruss_max call on this graph (0 if none) */
     int64_t peel_lists;    /* 1 if that call read precomputed per-edge triangle

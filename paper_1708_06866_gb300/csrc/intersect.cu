@@ -18,6 +18,7 @@
 // Graphs whose largest out-list exceeds the table capacity use k_edges_warp
 // (one warp per oriented edge, binary search in global memory).
 #include <algorithm>
+#include <atomic>
 #include <climits>
 
 #include "tc_internal.cuh"
@@ -339,13 +340,32 @@ size_t rows_smem(int log_cap, int mode) {
     return cap * 4 + cap * 2 + (mode == SUPPORT ? (cap / 2) * 4 : 0) + 16;
 }
 
+// The row kernel's dynamic shared memory depends on the graph.  The
+// function attribute that allows it is process-wide, so it is raised once
+// per device to the largest size any graph can need and never lowered:
+// concurrent calls on graphs of different sizes must not undercut each other.
+int ensure_rows_smem_limit() {
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    TC_CUDA_TRY(cudaGetDevice(&dev));
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load() & bit) return TC_OK;
+    int lc = 6;
+    while ((1 << lc) < 2 * RX_MAX_OUT) ++lc;
+    const int sm_max = (int)rows_smem(lc, SUPPORT);
+    TC_CUDA_TRY(cudaFuncSetAttribute(k_rows<COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_max));
+    TC_CUDA_TRY(cudaFuncSetAttribute(k_rows<SUPPORT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_max));
+    TC_CUDA_TRY(cudaFuncSetAttribute(k_rows<LISTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_max));
+    done.fetch_or(bit);
+    return TC_OK;
+}
+
 template <int MODE>
 int launch_rows(Graph* g, int32_t* sup, unsigned int* cursor, int2* pairs,
                 unsigned long long* partials, int blocks, cudaStream_t s) {
+    TC_TRY(ensure_rows_smem_limit());
     const int lc = rows_log_cap(g);
     const size_t sm = rows_smem(lc, MODE);
-    TC_CUDA_TRY(cudaFuncSetAttribute(k_rows<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sm));
     unsigned int* next_row = reinterpret_cast<unsigned int*>(g->dev_scalars + 4);
     TC_CUDA_TRY(cudaMemsetAsync(next_row, 0, sizeof(unsigned int), s));
     k_rows<MODE><<<blocks, RX_THREADS, sm, s>>>(g->rowptr, g->upper, g->col, g->eid, g->n, sup,
@@ -358,17 +378,17 @@ int rows_blocks(Graph* g, int mode) {
     int per_sm = 0;
     const size_t sm = rows_smem(rows_log_cap(g), mode);
     cudaError_t e = cudaSuccess;
-    if (mode == COUNT) {
-        cudaFuncSetAttribute(k_rows<COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (ensure_rows_smem_limit() != TC_OK) per_sm = 1;
+    else if (mode == COUNT)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows<COUNT>, RX_THREADS, sm);
-    } else if (mode == SUPPORT) {
-        cudaFuncSetAttribute(k_rows<SUPPORT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    else if (mode == SUPPORT)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows<SUPPORT>, RX_THREADS, sm);
-    } else {
-        cudaFuncSetAttribute(k_rows<LISTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows<LISTS>, RX_THREADS, sm);
+    if (e != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
     }
-    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     return num_sms() * per_sm;
 }
 

@@ -534,6 +534,8 @@ struct PeelPlan {
     unsigned long long* off = nullptr;
     int2* pairs = nullptr;
     ListsPlan lists;
+    bool build_lists = false;  // the lists are built by this peel (else cached)
+    bool keep_lists = false;   // ... and stay with the graph afterwards
     KernelTimer timer;
     PeelCtl result{};
 };
@@ -542,7 +544,7 @@ PeelPlan* peel_plan_new() { return new (std::nothrow) PeelPlan(); }
 void peel_plan_delete(PeelPlan* p) { delete p; }
 
 int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single, int32_t* t,
-              int form) {
+              int form, bool keep_lists) {
     PeelPlan& p = *pp;
     const int64_t m = g->m;
     if (!g->support_valid) return fail(TC_EINVAL, "internal: peel planned without supports");
@@ -568,9 +570,26 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
         TC_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
         p.tl = forced == PEEL_LISTS || need < 0.6 * (double)free_b;
     }
-    if (p.tl) {
-        TC_TRY(sc.alloc(&p.off, m + 1));
-        TC_TRY(sc.alloc(&p.pairs, std::max<int64_t>(1, 3 * g->triangles)));
+    if (p.tl && g->tri_valid) {
+        p.off = g->tri_off;  // built by an earlier peel of this graph
+        p.pairs = g->tri_pairs;
+        p.build_lists = false;
+        a.off = p.off;
+        a.pairs = p.pairs;
+    } else if (p.tl) {
+        p.build_lists = true;
+        p.keep_lists = keep_lists;
+        if (keep_lists) {
+            if (!g->tri_off) TC_TRY(dev_alloc_n(&g->tri_off, m + 1, g->last_stream));
+            if (!g->tri_pairs)
+                TC_TRY(dev_alloc_n(&g->tri_pairs, std::max<int64_t>(1, 3 * g->triangles),
+                                   g->last_stream));
+            p.off = g->tri_off;
+            p.pairs = g->tri_pairs;
+        } else {
+            TC_TRY(sc.alloc(&p.off, m + 1));
+            TC_TRY(sc.alloc(&p.pairs, std::max<int64_t>(1, 3 * g->triangles)));
+        }
         TC_TRY(plan_triangle_lists(g, sc, &p.lists));
         a.off = p.off;
         a.pairs = p.pairs;
@@ -610,7 +629,8 @@ int peel_enqueue(PeelPlan* pp, cudaStream_t s) {
     PeelArgs& a = p.a;
     const int64_t m = g->m;
     if (p.tl) {
-        TC_TRY(enqueue_triangle_lists(g, g->support, p.off, p.pairs, &p.lists, s));
+        if (p.build_lists)
+            TC_TRY(enqueue_triangle_lists(g, g->support, p.off, p.pairs, &p.lists, s));
     } else {
         TC_CUDA_TRY(cudaMemcpyAsync(a.col, g->col, sizeof(int32_t) * 2 * m,
                                     cudaMemcpyDeviceToDevice, s));
@@ -642,7 +662,7 @@ int peel_finish(PeelPlan* pp, cudaStream_t s, int64_t* n_alive, int32_t* kmax) {
     TC_CUDA_TRY(cudaStreamSynchronize(s));
     g->last_peel_rounds = r.rounds;
     g->stats.peel_ns = p.timer.elapsed_ns();
-    if (p.tl) g->stats.lists_ns = p.lists.timer.elapsed_ns();
+    g->stats.lists_ns = p.tl && p.build_lists ? p.lists.timer.elapsed_ns() : -1;
     // algorithmic bytes: a scanned entry reads its id, state and support
     // (12 B); a triangle-list entry is an 8-B pair, a neighbour-list entry
     // an id and an edge id (8 B); binary-search steps and state lookups read
@@ -652,6 +672,7 @@ int peel_finish(PeelPlan* pp, cudaStream_t s, int64_t* n_alive, int32_t* kmax) {
                           8 * (int64_t)r.lowered;
     if (r.abort) return fail(TC_ETIMEDOUT, "peel: a grid barrier wait ran out of time");
     if (r.overflow) return fail(TC_EOVERFLOW, "peel: round table exhausted");
+    if (p.build_lists && p.keep_lists) g->tri_valid = true;
     if (n_alive) *n_alive = r.n_alive;
     if (kmax) *kmax = r.kmax;
     return TC_OK;
@@ -667,7 +688,7 @@ int run_peel(Graph* g, int32_t k_first, bool single, int32_t* t, PeelCtl* result
     TC_TRY(ensure_support_impl(g, s));
     Scratch sc(s);
     PeelPlan p;
-    TC_TRY(peel_plan(&p, sc, g, k_first, single, t, PEEL_AUTO));
+    TC_TRY(peel_plan(&p, sc, g, k_first, single, t, PEEL_AUTO, /*keep_lists=*/true));
     TC_TRY(peel_enqueue(&p, s));
     TC_TRY(peel_finish(&p, s, nullptr, nullptr));
     *result = p.result;

@@ -8,6 +8,7 @@
 // look-back over a status array.  Every look-back wait is bounded in time;
 // a wait that runs out sets DEV_ERR_TIMEOUT and the block skips its writes.
 #include <algorithm>
+#include <atomic>
 #include <utility>
 
 #include "tc_internal.cuh"
@@ -230,15 +231,19 @@ int radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t*
     TC_LAUNCH_CHECK("k_bin_start");
 
     const bool has_val = vals != nullptr;
-    static bool attr_set = false;
-    if (!attr_set) {
+    // process-wide function attributes: set once per device (constant values)
+    static std::atomic<unsigned long long> attr_done{0};
+    int dev = 0;
+    TC_CUDA_TRY(cudaGetDevice(&dev));
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(attr_done.load() & bit)) {
         TC_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)dyn_smem(true)));
         TC_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)dyn_smem(false)));
-        attr_set = true;
+        attr_done.fetch_or(bit);
     }
     const int64_t spin = spin_limit_ns();
     uint64_t *ka = keys, *kb = keys_alt;

@@ -152,14 +152,10 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
 }
 
 inline int num_sms() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    return sms;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
 }
 
 inline int bits_for(uint64_t maxval) {  // bits needed to hold values 0..maxval (>= 1)
@@ -241,6 +237,11 @@ struct Graph {
     // cached support (edge-id order) and triangle count
     int32_t* support = nullptr;
     bool support_valid = false;
+    // cached per-edge triangle lists (kept after the first peel that builds
+    // them, when they fit): list of edge e = tri_pairs[tri_off[e] .. tri_off[e+1])
+    unsigned long long* tri_off = nullptr;
+    int2* tri_pairs = nullptr;
+    bool tri_valid = false;
     int64_t triangles = -1;
     int* dev_err = nullptr;
     unsigned long long* dev_scalars = nullptr;  // small device scratch (8 words)
@@ -265,8 +266,9 @@ int enqueue_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off
 struct PeelPlan;
 PeelPlan* peel_plan_new();
 void peel_plan_delete(PeelPlan* p);
+// keep_lists: a triangle-list build is kept with the graph for later peels.
 int peel_plan(PeelPlan* p, Scratch& sc, Graph* g, int32_t k_first, bool single, int32_t* t,
-              int form);
+              int form, bool keep_lists = false);
 int peel_enqueue(PeelPlan* p, cudaStream_t s);
 int peel_finish(PeelPlan* p, cudaStream_t s, int64_t* n_alive, int32_t* kmax);
 bool peel_uses_lists(const PeelPlan* p);
