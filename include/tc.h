@@ -229,6 +229,35 @@ typedef struct {
  * its graph), TC_EOVERFLOW, TC_ENOMEM, TC_ECUDA, TC_ETIMEDOUT. */
 int tc_batch_run(const tc_batch_desc* d, void* cuda_stream);
 
+/*
+ * tc_sort_keys_static — sorts n uint64 keys ascending, in place, by their low
+ * key_bits bits (an LSD radix sort, the library's own sort), WITHOUT
+ * ALLOCATING: no cudaMalloc, no stream-ordered allocation, no allocating
+ * library routine.  The paper has no counterpart; this entry point exists for
+ * callers that cannot allocate device memory where they call it — code whose
+ * device memory is owned by another allocator (e.g. a framework's caching
+ * pool that holds the free memory), code with a fixed pre-planned memory
+ * budget or a real-time deadline, code that must not enter the allocator.
+ *
+ * Scratch: one file-scope device array of TC_SORT_STATIC_SCRATCH_BYTES
+ * (about 8.5 MiB), which every GPU that loads the library holds until the
+ * process exits.  Limit: n <= TC_SORT_STATIC_MAX_KEYS (2^20); larger n
+ * returns TC_EOVERFLOW without touching the keys.
+ * keys: device memory of the caller, n entries (host pointers: TC_EINVAL).
+ * key_bits: 1..64; bits above key_bits are ignored by the ordering.
+ * The first call on a device sets the array up (looks up its device address
+ * and sets a kernel attribute) with that device current: make that first
+ * call before any stream capture.  Every call shares the one array and the
+ * array keeps the last call's contents (each call clears what must start at
+ * zero): calls whose work overlaps on the GPU — on different streams or
+ * threads without ordering between them — race and corrupt each other.
+ * Synchronises the stream (to report a device-side wait that ran out:
+ * TC_ETIMEDOUT).
+ */
+#define TC_SORT_STATIC_MAX_KEYS (1 << 20)
+#define TC_SORT_STATIC_SCRATCH_BYTES ((size_t)8929536)
+int tc_sort_keys_static(uint64_t* keys, int64_t n, int32_t key_bits, void* cuda_stream);
+
 /* Releases a graph (NULL is a no-op).  Synchronises the device's work on
  * the graph's last stream first. */
 void tc_graph_free(tc_graph* g);

@@ -9,6 +9,8 @@
 // a wait that runs out sets DEV_ERR_TIMEOUT and the block skips its writes.
 #include <algorithm>
 #include <atomic>
+#include <mutex>
+#include <string>
 #include <utility>
 
 #include "tc_internal.cuh"
@@ -268,6 +270,114 @@ int radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t*
     }
     return TC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Sorting without allocation.  tc_sort_keys_static is for callers that cannot
+// allocate device memory at the point of the call: code whose memory is
+// entirely owned by another allocator (a framework's caching pool holding
+// the free memory), code running where an allocation would break a
+// pre-planned memory budget or a real-time deadline, and code that must not
+// touch the device allocator at all.  Its scratch lives in one file-scope
+// device array of fixed size, shared by every call in the process.
+namespace {
+
+constexpr int64_t kStaticSortMaxKeys = int64_t(1) << 20;  // TC_SORT_STATIC_MAX_KEYS
+constexpr int64_t kStaticTiles = kStaticSortMaxKeys / RS_TILE;
+constexpr size_t kAltBytes = sizeof(uint64_t) * kStaticSortMaxKeys;
+constexpr size_t kStatusBytes = sizeof(uint64_t) * kStaticTiles * RADIX;
+constexpr size_t kHistBytes = sizeof(unsigned long long) * MAX_PASSES * RADIX;
+constexpr size_t kCtlBytes = 256;  // pass counters, then the error word
+constexpr size_t kStaticSortBytes = kAltBytes + kStatusBytes + kHistBytes + kCtlBytes;
+
+static_assert(kStaticSortMaxKeys == TC_SORT_STATIC_MAX_KEYS, "header limit");
+static_assert(kStaticSortBytes == TC_SORT_STATIC_SCRATCH_BYTES, "header scratch size");
+
+// Alt key buffer | tile status words | digit histograms | counters + error.
+static __device__ __align__(256) unsigned char g_sort_scratch[kStaticSortBytes];
+
+std::mutex g_static_mu;
+void* g_static_ptr[64] = {nullptr};  // device address of g_sort_scratch, per device
+
+// Once per device, with that device current: the array's device address (in
+// host code its name is only a host-side stand-in) and the kernels' shared
+// memory attribute.
+int static_sort_setup(int dev, unsigned char** out) {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (dev < 0 || dev >= 64) return fail(TC_EINVAL, "tc_sort_keys_static: device index");
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(TC_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        }
+        TC_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dyn_smem(false)));
+        g_static_ptr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_static_ptr[dev]);
+    return TC_OK;
+}
+
+}  // namespace
+
+}  // namespace tc
+
+extern "C" int tc_sort_keys_static(uint64_t* keys, int64_t n, int32_t key_bits,
+                                   void* cuda_stream) {
+    using namespace tc;
+    if (n < 0) return fail(TC_EINVAL, "tc_sort_keys_static: n < 0");
+    if (n > kStaticSortMaxKeys)
+        return fail(TC_EOVERFLOW, "tc_sort_keys_static: n exceeds TC_SORT_STATIC_MAX_KEYS (2^20); "
+                                  "use the allocating entry points for larger inputs");
+    if (key_bits < 1 || key_bits > 64) return fail(TC_EINVAL, "tc_sort_keys_static: key_bits");
+    if (n > 0 && !keys) return fail(TC_EINVAL, "tc_sort_keys_static: keys is NULL");
+    if (n > 0 && is_host_pointer(keys))
+        return fail(TC_EINVAL, "tc_sort_keys_static: keys must be device memory");
+    int dev = 0;
+    TC_CUDA_TRY(cudaGetDevice(&dev));
+    unsigned char* base = nullptr;
+    TC_TRY(static_sort_setup(dev, &base));
+    if (n <= 1) return TC_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    uint64_t* alt = reinterpret_cast<uint64_t*>(base);
+    uint64_t* status = reinterpret_cast<uint64_t*>(base + kAltBytes);
+    unsigned long long* hist =
+        reinterpret_cast<unsigned long long*>(base + kAltBytes + kStatusBytes);
+    unsigned int* counters =
+        reinterpret_cast<unsigned int*>(base + kAltBytes + kStatusBytes + kHistBytes);
+    int* err = reinterpret_cast<int*>(counters + MAX_PASSES);
+    const int passes = (key_bits + 7) / 8;
+    const int64_t tiles = (n + RS_TILE - 1) / RS_TILE;
+    // the array keeps the previous call's contents: clear what must start at zero
+    TC_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * passes * RADIX, s));
+    TC_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(uint64_t) * tiles * RADIX, s));
+    TC_CUDA_TRY(cudaMemsetAsync(counters, 0, kCtlBytes, s));
+    const int hblocks = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * 4);
+    k_histogram<<<hblocks, RS_BLOCK, 0, s>>>(keys, n, passes, hist);
+    TC_LAUNCH_CHECK("k_histogram");
+    k_bin_start<<<passes, 32, 0, s>>>(hist);
+    TC_LAUNCH_CHECK("k_bin_start");
+    const int64_t spin = spin_limit_ns();
+    uint64_t *ka = keys, *kb = alt;
+    for (int p = 0; p < passes; ++p) {
+        k_onesweep<false><<<(unsigned)tiles, RS_BLOCK, dyn_smem(false), s>>>(
+            ka, kb, nullptr, nullptr, n, p, hist + p * RADIX, status, counters + p, err, spin);
+        TC_LAUNCH_CHECK("k_onesweep");
+        std::swap(ka, kb);
+    }
+    if (ka != keys)
+        TC_CUDA_TRY(cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+    int h = 0;
+    TC_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h & DEV_ERR_TIMEOUT) return fail(TC_ETIMEDOUT, "tc_sort_keys_static: a wait ran out of time");
+    if (h) return fail(TC_ECUDA, "tc_sort_keys_static: internal bounds check failed");
+    return TC_OK;
+}
+
+namespace tc {
 
 int scan_block_totals(uint32_t* totals, int64_t count, uint64_t* grand_total_dev,
                       cudaStream_t s) {
