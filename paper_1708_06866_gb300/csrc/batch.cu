@@ -72,11 +72,10 @@ __global__ void k_graph_edge_ranges(const int32_t* __restrict__ lo, int64_t m,
     }
 }
 
-// Per-graph sums over contiguous edge ranges, one warp per graph:
-// MODE 0: sum of supports / 3 (triangles); MODE 1: edges with state 0
-// (k-truss survivors).
-template <int MODE>
-__global__ void k_segment_sums(const int32_t* __restrict__ x, const int64_t* __restrict__ ge,
+// Per-graph sums over contiguous canonical edge ranges, one warp per graph:
+// MODE 0: sum of supports / 3 (triangles); MODE 1: k-truss mask bytes.
+template <int MODE, typename T>
+__global__ void k_segment_sums(const T* __restrict__ x, const int64_t* __restrict__ ge,
                                int32_t G, long long* __restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -84,7 +83,7 @@ __global__ void k_segment_sums(const int32_t* __restrict__ x, const int64_t* __r
     for (int64_t g = w0; g < G; g += nw) {
         unsigned long long acc = 0;
         for (int64_t e = ge[g] + lane; e < ge[g + 1]; e += 32)
-            acc += MODE == 0 ? (unsigned long long)x[e] : (x[e] == 0 ? 1ull : 0ull);
+            acc += (unsigned long long)x[e];
         acc = warp_sum(acc);
         if (lane == 0) out[g] = MODE == 0 ? (long long)(acc / 3) : (long long)acc;
     }
@@ -251,6 +250,10 @@ int batch_run(const tc_batch_desc* d, cudaStream_t user_stream) {
     Scratch sc(s);
     int64_t *voff_d, *ge;
     long long *tri_d, *left_d;
+    int32_t* sup_can;       // supports in canonical order (graphs are contiguous there)
+    uint8_t* mask_can;      // k-truss mask in canonical order
+    TC_TRY(sc.alloc(&sup_can, g.m));
+    TC_TRY(sc.alloc(&mask_can, g.m));
     TC_TRY(sc.alloc(&voff_d, G + 1));
     TC_TRY(sc.alloc(&ge, G + 1));
     TC_TRY(sc.alloc(&tri_d, G));
@@ -311,14 +314,18 @@ int batch_run(const tc_batch_desc* d, cudaStream_t user_stream) {
     auto enqueue_query = [&]() -> int {
         if (g.m > 0) {
             TC_TRY(compute_support(&g, g.support, true, nullptr, s, choice.intersect));
-            k_segment_sums<0><<<grid_items((int64_t)G * 32), 256, 0, s>>>(g.support, ge, G, tri_d);
+            TC_TRY(to_canonical_i32(g.support, g.fwd, g.m, sup_can, s));
+            k_segment_sums<0, int32_t><<<grid_items((int64_t)G * 32), 256, 0, s>>>(sup_can, ge, G,
+                                                                                  tri_d);
             TC_LAUNCH_CHECK("k_segment_sums");
         } else {
             TC_CUDA_TRY(cudaMemsetAsync(tri_d, 0, sizeof(long long) * G, s));
         }
         if (peel) {
             TC_TRY(peel_enqueue(plan, s));
-            k_segment_sums<1><<<grid_items((int64_t)G * 32), 256, 0, s>>>(t, ge, G, left_d);
+            TC_TRY(mask_from_state(t, g.fwd, g.m, mask_can, s));
+            k_segment_sums<1, uint8_t><<<grid_items((int64_t)G * 32), 256, 0, s>>>(mask_can, ge, G,
+                                                                                  left_d);
             TC_LAUNCH_CHECK("k_segment_sums");
         }
         return TC_OK;

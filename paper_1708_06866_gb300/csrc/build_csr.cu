@@ -227,6 +227,27 @@ __global__ void k_row_stats(const int64_t* __restrict__ rowptr, const int64_t* _
     }
 }
 
+// Internal edge ids: position in the oriented (u, v) order.  fwd[j] is the
+// canonical id of internal edge j; inv is its inverse.
+__global__ void k_invert(const int32_t* __restrict__ fwd, int64_t m, int32_t* __restrict__ inv) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
+        inv[fwd[j]] = (int32_t)j;
+}
+
+__global__ void k_relabel(int32_t* __restrict__ eid, int64_t nnz, const int32_t* __restrict__ inv) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += stride)
+        eid[i] = inv[eid[i]];
+}
+
+__global__ void k_gather_ends(const int2* __restrict__ ends, const int32_t* __restrict__ fwd,
+                              int64_t m, int2* __restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
+        out[j] = ends[fwd[j]];
+}
+
 inline unsigned grid_for(int64_t n, int threads = 256) {
     const int64_t cap = (int64_t)num_sms() * 32;
     int64_t b = (n + threads - 1) / threads;
@@ -337,6 +358,21 @@ int build_graph(Graph* g, const int32_t* src, const int32_t* dst, cudaStream_t s
             UpperOp up{pkeys, pvals, bits, g->fwd};
             TC_TRY(compact(up, nnz, &cnt, scalar, s));
             if (cnt != m) return fail(TC_ECUDA, "internal: oriented edge count mismatch");
+            // renumber edges in oriented order: a row's edges become contiguous,
+            // so per-edge arrays indexed by these ids are read and updated with
+            // locality (canonical ids are restored at the ABI boundary)
+            int32_t* inv;
+            int2* ends2;
+            TC_TRY(sc.alloc(&inv, m));
+            TC_TRY(dev_alloc_n(&ends2, m, s));
+            k_invert<<<grid_for(m), 256, 0, s>>>(g->fwd, m, inv);
+            TC_LAUNCH_CHECK("k_invert");
+            k_relabel<<<grid_for(nnz), 256, 0, s>>>(g->eid, nnz, inv);
+            TC_LAUNCH_CHECK("k_relabel");
+            k_gather_ends<<<grid_for(m), 256, 0, s>>>(g->ends, g->fwd, m, ends2);
+            TC_LAUNCH_CHECK("k_gather_ends");
+            dev_free(g->ends, s);
+            g->ends = ends2;
         }
         TC_CUDA_TRY(cudaMemsetAsync(g->dev_scalars, 0, 2 * sizeof(unsigned long long), s));
         k_row_stats<<<grid_for(n), 256, 0, s>>>(g->rowptr, g->upper, n, g->dev_scalars);

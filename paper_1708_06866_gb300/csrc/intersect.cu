@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
 // elements and look each up in the longer list by binary search.
 template <bool SUPPORT>
 __global__ void __launch_bounds__(IX_THREADS) k_edges_warp(
-    const int32_t* __restrict__ fwd, const int2* __restrict__ ends,
+    const int2* __restrict__ ends,
     const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
     const int32_t* __restrict__ col, const int32_t* __restrict__ eid, int64_t m,
     int32_t* __restrict__ sup, unsigned long long* __restrict__ partials) {
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(IX_THREADS) k_edges_warp(
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long acc = 0;
     for (int64_t j = wid; j < m; j += nw) {
-        const int32_t e = fwd[j];
+        const int32_t e = (int32_t)j;
         const int2 uv = ends[e];
         int64_t s0 = upper[uv.x], s1 = rowptr[uv.x + 1];
         int64_t l0 = upper[uv.y], l1 = rowptr[uv.y + 1];
@@ -218,13 +218,13 @@ __global__ void __launch_bounds__(1024) k_reduce_partials(const unsigned long lo
     }
 }
 
-__global__ void k_wedge_work(const int32_t* __restrict__ fwd, const int2* __restrict__ ends,
+__global__ void k_wedge_work(const int2* __restrict__ ends,
                              const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
                              int64_t m, unsigned long long* __restrict__ out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long acc = 0;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
-        const int2 uv = ends[fwd[j]];
+        const int2 uv = ends[j];
         acc += (unsigned long long)(rowptr[uv.x + 1] - upper[uv.x]) +
                (unsigned long long)(rowptr[uv.y + 1] - upper[uv.y]);
     }
@@ -399,7 +399,7 @@ int graph_wedge_work(Graph* g, int64_t* out, cudaStream_t s) {
         unsigned long long h = 0;
         if (g->m > 0) {
             TC_CUDA_TRY(cudaMemsetAsync(g->dev_scalars + 2, 0, sizeof(unsigned long long), s));
-            k_wedge_work<<<num_sms() * 8, 256, 0, s>>>(g->fwd, g->ends, g->rowptr, g->upper, g->m,
+            k_wedge_work<<<num_sms() * 8, 256, 0, s>>>(g->ends, g->rowptr, g->upper, g->m,
                                                        g->dev_scalars + 2);
             TC_LAUNCH_CHECK("k_wedge_work");
             TC_CUDA_TRY(cudaMemcpyAsync(&h, g->dev_scalars + 2, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -432,11 +432,11 @@ int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangle
             TC_TRY(launch_rows<SUPPORT>(g, sup, nullptr, nullptr, partials, blocks, s));
         else TC_TRY(launch_rows<COUNT>(g, nullptr, nullptr, nullptr, partials, blocks, s));
     } else if (want_support) {
-        k_edges_warp<true><<<blocks, IX_THREADS, 0, s>>>(g->fwd, g->ends, g->rowptr, g->upper,
+        k_edges_warp<true><<<blocks, IX_THREADS, 0, s>>>(g->ends, g->rowptr, g->upper,
                                                          g->col, g->eid, m, sup, partials);
         TC_LAUNCH_CHECK("k_edges_warp");
     } else {
-        k_edges_warp<false><<<blocks, IX_THREADS, 0, s>>>(g->fwd, g->ends, g->rowptr, g->upper,
+        k_edges_warp<false><<<blocks, IX_THREADS, 0, s>>>(g->ends, g->rowptr, g->upper,
                                                           g->col, g->eid, m, nullptr, partials);
         TC_LAUNCH_CHECK("k_edges_warp");
     }
@@ -454,6 +454,24 @@ int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangle
 }
 
 bool triangle_lists_supported(const Graph* g) { return g->max_out <= RX_MAX_OUT; }
+
+namespace {
+__global__ void k_scatter_i32(const int32_t* __restrict__ in, const int32_t* __restrict__ fwd,
+                              int64_t m, int32_t* __restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
+        out[fwd[j]] = in[j];
+}
+}  // namespace
+
+int to_canonical_i32(const int32_t* in, const int32_t* fwd, int64_t m, int32_t* out,
+                     cudaStream_t s) {
+    if (m == 0) return TC_OK;
+    k_scatter_i32<<<(unsigned)std::min<int64_t>((m + 255) / 256, (int64_t)num_sms() * 16), 256, 0,
+                    s>>>(in, fwd, m, out);
+    TC_LAUNCH_CHECK("k_scatter_i32");
+    return TC_OK;
+}
 
 int plan_triangle_lists(Graph* g, Scratch& sc, ListsPlan* lp) {
     const int64_t m = g->m;

@@ -484,21 +484,24 @@ __global__ void k_peel_init(const int64_t* __restrict__ rowptr, int32_t n,
         rowlen[r] = (int32_t)(rowptr[r + 1] - rowptr[r]);
 }
 
-// Final states -> outputs: the k-truss mask (alive = 0) or truss numbers
-// (an edge removed in a round of level k has truss number k - 1).
-__global__ void k_mask_from_state(const int32_t* __restrict__ t, int64_t m,
+// Final states -> canonical-order outputs: the k-truss mask (alive = 0) or
+// truss numbers (an edge removed in a round of level k has truss number k - 1).
+__global__ void k_mask_from_state(const int32_t* __restrict__ t,
+                                  const int32_t* __restrict__ fwd, int64_t m,
                                   uint8_t* __restrict__ mask) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
-        mask[e] = t[e] == 0 ? 1 : 0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
+        mask[fwd[j]] = t[j] == 0 ? 1 : 0;
 }
 
-__global__ void k_truss_from_state(int32_t* __restrict__ t, int64_t m,
-                                   const int32_t* __restrict__ level_of) {
+__global__ void k_truss_from_state(const int32_t* __restrict__ t,
+                                   const int32_t* __restrict__ fwd, int64_t m,
+                                   const int32_t* __restrict__ level_of,
+                                   int32_t* __restrict__ truss) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-        const int32_t st = t[e];
-        t[e] = st < 0 ? level_of[-st] - 1 : 0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        const int32_t st = t[j];
+        truss[fwd[j]] = st < 0 ? level_of[-st] - 1 : 0;
     }
 }
 
@@ -534,6 +537,8 @@ struct PeelPlan {
     unsigned long long* off = nullptr;
     int2* pairs = nullptr;
     ListsPlan lists;
+    uint8_t* out_mask = nullptr;    // single level: canonical k-truss mask
+    int32_t* out_truss = nullptr;   // decomposition: canonical truss numbers
     bool build_lists = false;  // the lists are built by this peel (else cached)
     bool keep_lists = false;   // ... and stay with the graph afterwards
     KernelTimer timer;
@@ -647,9 +652,13 @@ int peel_enqueue(PeelPlan* pp, cudaStream_t s) {
     TC_CUDA_TRY(cudaLaunchCooperativeKernel(p.fn, dim3(p.blocks), dim3(PK_THREADS), params, 0, s));
     count_launch();
     TC_TRY(p.timer.stop(s));
-    if (!p.single) {
-        k_truss_from_state<<<small_grid(m), 256, 0, s>>>(a.t, m, a.level_of);
+    if (!p.single && p.out_truss) {
+        k_truss_from_state<<<small_grid(m), 256, 0, s>>>(a.t, g->fwd, m, a.level_of, p.out_truss);
         TC_LAUNCH_CHECK("k_truss_from_state");
+    }
+    if (p.single && p.out_mask) {
+        k_mask_from_state<<<small_grid(m), 256, 0, s>>>(a.t, g->fwd, m, p.out_mask);
+        TC_LAUNCH_CHECK("k_mask_from_state");
     }
     return TC_OK;
 }
@@ -682,13 +691,18 @@ bool peel_uses_lists(const PeelPlan* p) { return p->tl; }
 
 namespace {
 
-// Plan, run and complete one peel on the graph's stream.
-int run_peel(Graph* g, int32_t k_first, bool single, int32_t* t, PeelCtl* result,
-             cudaStream_t s) {
+// Plan, run and complete one peel on the graph's stream; results go to the
+// canonical-order output (mask for one level, truss numbers otherwise).
+int run_peel(Graph* g, int32_t k_first, bool single, uint8_t* out_mask, int32_t* out_truss,
+             PeelCtl* result, cudaStream_t s) {
     TC_TRY(ensure_support_impl(g, s));
     Scratch sc(s);
+    int32_t* t;
+    TC_TRY(sc.alloc(&t, g->m));
     PeelPlan p;
     TC_TRY(peel_plan(&p, sc, g, k_first, single, t, PEEL_AUTO, /*keep_lists=*/true));
+    p.out_mask = out_mask;
+    p.out_truss = out_truss;
     TC_TRY(peel_enqueue(&p, s));
     TC_TRY(peel_finish(&p, s, nullptr, nullptr));
     *result = p.result;
@@ -699,8 +713,9 @@ int run_peel(Graph* g, int32_t k_first, bool single, int32_t* t, PeelCtl* result
 
 int ensure_support(Graph* g, cudaStream_t s) { return ensure_support_impl(g, s); }
 
-int mask_from_state(const int32_t* t, int64_t m, uint8_t* mask, cudaStream_t s) {
-    k_mask_from_state<<<small_grid(m), 256, 0, s>>>(t, m, mask);
+int mask_from_state(const int32_t* t, const int32_t* fwd, int64_t m, uint8_t* mask,
+                    cudaStream_t s) {
+    k_mask_from_state<<<small_grid(m), 256, 0, s>>>(t, fwd, m, mask);
     TC_LAUNCH_CHECK("k_mask_from_state");
     return TC_OK;
 }
@@ -711,12 +726,8 @@ int peel_ktruss(Graph* g, int32_t k, uint8_t* mask, int64_t* edges_left, cudaStr
         if (edges_left) *edges_left = 0;
         return TC_OK;
     }
-    Scratch sc(s);
-    int32_t* t;
-    TC_TRY(sc.alloc(&t, m));
     PeelCtl r{};
-    TC_TRY(run_peel(g, k, true, t, &r, s));
-    TC_TRY(mask_from_state(t, m, mask, s));
+    TC_TRY(run_peel(g, k, true, mask, nullptr, &r, s));
     if (edges_left) *edges_left = r.n_alive;
     return TC_OK;
 }
@@ -727,7 +738,7 @@ int peel_decompose(Graph* g, int32_t* truss, int32_t* kmax, cudaStream_t s) {
         return TC_OK;
     }
     PeelCtl r{};
-    TC_TRY(run_peel(g, 3, false, truss, &r, s));
+    TC_TRY(run_peel(g, 3, false, nullptr, truss, &r, s));
     *kmax = r.kmax;
     return TC_OK;
 }

@@ -243,7 +243,15 @@ int tc_edge_support(tc_graph* g, int32_t* support_out, int64_t* triangles_out,
         gg->triangles = T;
         *triangles_out = T;
     }
-    return deliver(support_out, gg->support, gg->m, s);
+    // the cached supports are in internal edge order: scatter to edge ids
+    if (gg->m == 0) return TC_OK;
+    if (!tc::is_host_pointer(support_out))
+        return tc::to_canonical_i32(gg->support, gg->fwd, gg->m, support_out, s);
+    tc::Scratch sc(s);
+    int32_t* tmp;
+    TC_TRY(sc.alloc(&tmp, gg->m));
+    TC_TRY(tc::to_canonical_i32(gg->support, gg->fwd, gg->m, tmp, s));
+    return deliver(support_out, tmp, gg->m, s);
 }
 
 int ktruss(tc_graph* g, int32_t k, uint8_t* mask_out, int64_t* edges_out, void* cuda_stream) {

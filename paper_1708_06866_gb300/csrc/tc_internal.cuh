@@ -216,15 +216,18 @@ struct Graph {
     // canonical edge list (original ids), edge-id order
     int32_t* lo = nullptr;
     int32_t* hi = nullptr;
-    // endpoints in rank ids, (min, max), edge-id order
+    // Internal edge ids: j = position in the oriented (u, v) order, u < v in
+    // rank; fwd[j] is its canonical id (the ABI's edge id).  Everything below
+    // that is per edge is in internal order.
+    // endpoints in rank ids, (u, v), internal order
     int2* ends = nullptr;
     // symmetric CSR over rank ids: row r = [rowptr[r], rowptr[r+1]); its part
     // above r (the oriented out-list N+(r)) starts at upper[r]
     int64_t* rowptr = nullptr;
     int64_t* upper = nullptr;
     int32_t* col = nullptr;   // 2m neighbour rank ids
-    int32_t* eid = nullptr;   // 2m edge ids
-    int32_t* fwd = nullptr;   // m edge ids in oriented (u, v) order
+    int32_t* eid = nullptr;   // 2m internal edge ids
+    int32_t* fwd = nullptr;   // canonical id of each internal edge
     int32_t max_out = 0;      // max |N+(u)|
     int32_t max_deg = 0;
     int64_t wedge_work = -1;  // sum of |N+(u)| + |N+(v)| over oriented edges (lazy)
@@ -234,7 +237,7 @@ struct Graph {
         int64_t count_ns = -1, support_ns = -1, lists_ns = -1, peel_ns = -1;
         int64_t peel_bytes = -1;
     } stats;  // device time of the latest launch of each main kernel
-    // cached support (edge-id order) and triangle count
+    // cached support (internal order) and triangle count
     int32_t* support = nullptr;
     bool support_valid = false;
     // cached per-edge triangle lists (kept after the first peel that builds
@@ -273,7 +276,12 @@ int peel_enqueue(PeelPlan* p, cudaStream_t s);
 int peel_finish(PeelPlan* p, cudaStream_t s, int64_t* n_alive, int32_t* kmax);
 bool peel_uses_lists(const PeelPlan* p);
 int ensure_support(Graph* g, cudaStream_t s);
-int mask_from_state(const int32_t* t, int64_t m, uint8_t* mask, cudaStream_t s);
+// Internal-order per-edge arrays -> canonical order (out[fwd[j]] = in[j]).
+int to_canonical_i32(const int32_t* in, const int32_t* fwd, int64_t m, int32_t* out,
+                     cudaStream_t s);
+// k-truss mask in canonical order from internal edge states (alive = 0).
+int mask_from_state(const int32_t* t, const int32_t* fwd, int64_t m, uint8_t* mask,
+                    cudaStream_t s);
 
 int build_graph(Graph* g, const int32_t* src_d, const int32_t* dst_d, cudaStream_t s);
 void free_graph(Graph* g);
