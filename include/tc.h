@@ -109,8 +109,12 @@ int tc_edge_support(tc_graph* g, int32_t* support_out, int64_t* triangles_out,
  * edges sharing their triangles are lowered, until no edge is below
  * (Algorithm 4's loop).  k >= 2 (k = 2 keeps every edge).
  * The graph keeps the supports, and the per-edge triangle lists when the
- * peel builds them and they fit, for later ktruss / ktruss_max calls
- * (tc_graph_info's device_bytes counts them).
+ * peel builds them and they fit, for later ktruss / ktruss_max calls, and
+ * the result of the latest ktruss call: a later ktruss with a k at least as
+ * large continues from that truss instead of the whole graph (Section
+ * III-B's procedure of passing the k-truss on to the next k; the (k+1)-truss
+ * lies inside the k-truss, so the result is the same).  tc_graph_info's
+ * device_bytes counts what the graph keeps.
  * mask_out: m uint8 in edge-id order, 1 = in the k-truss (device or host).
  * edges_out: host int64, number of edges in the k-truss; may be NULL.
  * Errors: TC_EINVAL for k < 2.

@@ -82,6 +82,7 @@ struct PeelArgs {
     const unsigned long long* off;  // triangle-list mode: list of edge e = pairs[off[e]..off[e+1])
     const int2* pairs;              // the two other edges of each triangle through e
     int32_t k_first;
+    int32_t r_first;  // first round number (2 when resuming: state -1 = removed before)
     int32_t single;  // 1: peel level k_first only
     int64_t spin_ns;
 };
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
     int64_t rounds = 0, compactions = 0, fulls = 0;
     int32_t k = a.k_first;
     int32_t kmax = 2;
-    int32_t r = 1;  // round whose frontier the next level scan collects
+    int32_t r = a.r_first;  // round whose frontier the next level scan collects
     int32_t bound = INT_MIN;
     int level = 0;
     Tally tl;
@@ -494,6 +495,12 @@ __global__ void k_mask_from_state(const int32_t* __restrict__ t,
         mask[fwd[j]] = t[j] == 0 ? 1 : 0;
 }
 
+__global__ void k_resume_states(int32_t* __restrict__ t, int64_t m) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
+        if (t[j] != 0) t[j] = -1;
+}
+
 __global__ void k_truss_from_state(const int32_t* __restrict__ t,
                                    const int32_t* __restrict__ fwd, int64_t m,
                                    const int32_t* __restrict__ level_of,
@@ -537,6 +544,9 @@ struct PeelPlan {
     unsigned long long* off = nullptr;
     int2* pairs = nullptr;
     ListsPlan lists;
+    bool resume = false;       // start from the graph's cached k-truss
+    bool cache = false;        // state/support (and adjacency) are the graph's cache
+    bool fresh_adj = true;     // the working adjacency must be copied from the graph
     uint8_t* out_mask = nullptr;    // single level: canonical k-truss mask
     int32_t* out_truss = nullptr;   // decomposition: canonical truss numbers
     bool build_lists = false;  // the lists are built by this peel (else cached)
@@ -549,7 +559,7 @@ PeelPlan* peel_plan_new() { return new (std::nothrow) PeelPlan(); }
 void peel_plan_delete(PeelPlan* p) { delete p; }
 
 int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single, int32_t* t,
-              int form, bool keep_lists) {
+              int form, bool keep_lists, bool use_cache) {
     PeelPlan& p = *pp;
     const int64_t m = g->m;
     if (!g->support_valid) return fail(TC_EINVAL, "internal: peel planned without supports");
@@ -563,8 +573,17 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
     a.rowptr = g->rowptr;
     a.t = t;
     a.k_first = k_first;
+    a.r_first = 1;
     a.single = single ? 1 : 0;
     a.spin_ns = spin_limit_ns();
+    p.cache = single && use_cache;
+    p.resume = p.cache && g->kt_k > 0 && k_first >= g->kt_k;
+    if (p.cache) {
+        if (!g->kt_state) TC_TRY(dev_alloc_n(&g->kt_state, m, g->last_stream));
+        if (!g->kt_support) TC_TRY(dev_alloc_n(&g->kt_support, m, g->last_stream));
+        a.t = g->kt_state;
+        if (!p.resume) g->kt_k = 0;  // rebuilt below; valid again only if this peel completes
+    }
     const int forced = form != PEEL_AUTO ? form : peel_mode();
     p.tl = false;
     // list positions are 32-bit: the triangle-list form needs 3T < 2^32
@@ -598,12 +617,35 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
         TC_TRY(plan_triangle_lists(g, sc, &p.lists));
         a.off = p.off;
         a.pairs = p.pairs;
+    } else if (p.cache) {
+        // the compacted adjacency stays with the graph when it fits
+        p.fresh_adj = !(p.resume && g->kt_adj);
+        size_t free_b = 0, total_b = 0;
+        TC_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        const bool room = g->kt_col || (double)(16 * m + 4 * (int64_t)g->n) < 0.4 * (double)free_b;
+        if (room) {
+            if (!g->kt_col) {
+                TC_TRY(dev_alloc_n(&g->kt_col, 2 * m, g->last_stream));
+                TC_TRY(dev_alloc_n(&g->kt_eid, 2 * m, g->last_stream));
+                TC_TRY(dev_alloc_n(&g->kt_rowlen, g->n, g->last_stream));
+            }
+            a.col = g->kt_col;
+            a.eid = g->kt_eid;
+            a.rowlen = g->kt_rowlen;
+        } else {
+            p.fresh_adj = true;
+            TC_TRY(sc.alloc(&a.rowlen, g->n));
+            TC_TRY(sc.alloc(&a.col, 2 * m));
+            TC_TRY(sc.alloc(&a.eid, 2 * m));
+        }
+        g->kt_adj = false;  // valid again only if this peel completes in the graph's buffers
     } else {
         TC_TRY(sc.alloc(&a.rowlen, g->n));
         TC_TRY(sc.alloc(&a.col, 2 * m));
         TC_TRY(sc.alloc(&a.eid, 2 * m));
     }
-    TC_TRY(sc.alloc(&a.s, m));
+    if (p.cache) a.s = g->kt_support;
+    else TC_TRY(sc.alloc(&a.s, m));
     for (int i = 0; i < 2; ++i) {
         TC_TRY(sc.alloc(&a.A[i], m));
         TC_TRY(sc.alloc(&a.W[i], m));
@@ -636,7 +678,7 @@ int peel_enqueue(PeelPlan* pp, cudaStream_t s) {
     if (p.tl) {
         if (p.build_lists)
             TC_TRY(enqueue_triangle_lists(g, g->support, p.off, p.pairs, &p.lists, s));
-    } else {
+    } else if (p.fresh_adj) {
         TC_CUDA_TRY(cudaMemcpyAsync(a.col, g->col, sizeof(int32_t) * 2 * m,
                                     cudaMemcpyDeviceToDevice, s));
         TC_CUDA_TRY(cudaMemcpyAsync(a.eid, g->eid, sizeof(int32_t) * 2 * m,
@@ -644,8 +686,17 @@ int peel_enqueue(PeelPlan* pp, cudaStream_t s) {
         k_peel_init<<<small_grid(g->n), 256, 0, s>>>(g->rowptr, g->n, a.rowlen);
         TC_LAUNCH_CHECK("k_peel_init");
     }
-    TC_CUDA_TRY(cudaMemcpyAsync(a.s, g->support, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
-    TC_CUDA_TRY(cudaMemsetAsync(a.t, 0, sizeof(int32_t) * m, s));
+    if (p.resume) {
+        // edges outside the cached truss count as removed before round 2;
+        // the cached supports are already those within the truss
+        k_resume_states<<<small_grid(m), 256, 0, s>>>(a.t, m);
+        TC_LAUNCH_CHECK("k_resume_states");
+        a.r_first = 2;
+    } else {
+        TC_CUDA_TRY(cudaMemcpyAsync(a.s, g->support, sizeof(int32_t) * m,
+                                    cudaMemcpyDeviceToDevice, s));
+        TC_CUDA_TRY(cudaMemsetAsync(a.t, 0, sizeof(int32_t) * m, s));
+    }
     TC_CUDA_TRY(cudaMemsetAsync(a.ctl, 0, sizeof(PeelCtl), s));
     void* params[] = {&a};
     TC_TRY(p.timer.start(s));
@@ -682,6 +733,10 @@ int peel_finish(PeelPlan* pp, cudaStream_t s, int64_t* n_alive, int32_t* kmax) {
     if (r.abort) return fail(TC_ETIMEDOUT, "peel: a grid barrier wait ran out of time");
     if (r.overflow) return fail(TC_EOVERFLOW, "peel: round table exhausted");
     if (p.build_lists && p.keep_lists) g->tri_valid = true;
+    if (p.cache) {
+        g->kt_k = p.a.k_first;
+        g->kt_adj = !p.tl && p.a.col == g->kt_col && g->kt_col != nullptr;
+    }
     if (n_alive) *n_alive = r.n_alive;
     if (kmax) *kmax = r.kmax;
     return TC_OK;
@@ -700,7 +755,8 @@ int run_peel(Graph* g, int32_t k_first, bool single, uint8_t* out_mask, int32_t*
     int32_t* t;
     TC_TRY(sc.alloc(&t, g->m));
     PeelPlan p;
-    TC_TRY(peel_plan(&p, sc, g, k_first, single, t, PEEL_AUTO, /*keep_lists=*/true));
+    TC_TRY(peel_plan(&p, sc, g, k_first, single, t, PEEL_AUTO, /*keep_lists=*/true,
+                     /*use_cache=*/single));
     p.out_mask = out_mask;
     p.out_truss = out_truss;
     TC_TRY(peel_enqueue(&p, s));

@@ -113,6 +113,11 @@ void free_graph(Graph* g) {
     dev_free(g->support, s);
     dev_free(g->tri_off, s);
     dev_free(g->tri_pairs, s);
+    dev_free(g->kt_state, s);
+    dev_free(g->kt_support, s);
+    dev_free(g->kt_col, s);
+    dev_free(g->kt_eid, s);
+    dev_free(g->kt_rowlen, s);
     dev_free(g->dev_err, s);
     dev_free(g->dev_scalars, s);
     cudaStreamSynchronize(s);
@@ -317,7 +322,8 @@ int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream) {
     const int64_t m = gg->m, n = gg->n;
     info->device_bytes = m * (4 + 4 + 8 + 4 + 4 + 4) + 8 * (n + 1) + 8 * n +
                          (gg->support ? 4 * m : 0) +
-                         (gg->tri_valid ? 8 * (m + 1) + 24 * gg->triangles : 0);
+                         (gg->tri_valid ? 8 * (m + 1) + 24 * gg->triangles : 0) +
+                         (gg->kt_state ? 8 * m : 0) + (gg->kt_col ? 16 * m + 4 * n : 0);
     info->peel_rounds = gg->last_peel_rounds;
     info->peel_lists = gg->last_peel_lists ? 1 : 0;
     info->count_kernel_ns = gg->stats.count_ns;

@@ -245,6 +245,17 @@ struct Graph {
     unsigned long long* tri_off = nullptr;
     int2* tri_pairs = nullptr;
     bool tri_valid = false;
+    // the latest single-level k-truss (ktruss): internal edge states (0 = in
+    // the truss), supports within it and, for the intersection form, its
+    // compacted adjacency; a later ktruss with a k at least as large resumes
+    // from it (the (k+1)-truss lies inside the k-truss)
+    int32_t* kt_state = nullptr;
+    int32_t* kt_support = nullptr;
+    int32_t kt_k = 0;  // 0 = nothing cached
+    int32_t* kt_col = nullptr;
+    int32_t* kt_eid = nullptr;
+    int32_t* kt_rowlen = nullptr;
+    bool kt_adj = false;
     int64_t triangles = -1;
     int* dev_err = nullptr;
     unsigned long long* dev_scalars = nullptr;  // small device scratch (8 words)
@@ -269,9 +280,11 @@ int enqueue_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off
 struct PeelPlan;
 PeelPlan* peel_plan_new();
 void peel_plan_delete(PeelPlan* p);
-// keep_lists: a triangle-list build is kept with the graph for later peels.
+// keep_lists: a triangle-list build is kept with the graph for later peels;
+// use_cache (single level only): work in the graph's k-truss cache and
+// resume from it when k is at least the cached k.
 int peel_plan(PeelPlan* p, Scratch& sc, Graph* g, int32_t k_first, bool single, int32_t* t,
-              int form, bool keep_lists = false);
+              int form, bool keep_lists = false, bool use_cache = false);
 int peel_enqueue(PeelPlan* p, cudaStream_t s);
 int peel_finish(PeelPlan* p, cudaStream_t s, int64_t* n_alive, int32_t* kmax);
 bool peel_uses_lists(const PeelPlan* p);

@@ -55,9 +55,12 @@ def gpu_all(src, dst, n, ks=(2, 3, 4, 5, 6)):
         prev = tc.tc_debug_peel_mode(mode)
         try:
             masks = {}
-            for k in ks:
+            for k in ks:                    # ascending: each call resumes from the last
                 mk, c = tc.ktruss(g, k)
                 masks[k] = (mk.cpu().numpy(), c)
+            for k in sorted(ks, reverse=True):   # descending: fresh peels, same trusses
+                mk, c = tc.ktruss(g, k)
+                assert c == masks[k][1] and np.array_equal(mk.cpu().numpy(), masks[k][0]), k
             kmax, truss = tc.ktruss_max(g)
             info = tc.tc_graph_info(g)
         finally:
