@@ -37,6 +37,28 @@ __device__ __forceinline__ uint32_t slot_of(int32_t w, int log_cap) {
     return ((uint32_t)w * 0x9E3779B1u) >> (32 - log_cap);
 }
 
+// Table size for an out-list of du entries: load <= 1/4 up to 1024 entries
+// (short probe runs: a warp waits for its slowest lane), <= 1/2 above.
+__host__ __device__ __forceinline__ int table_log_cap(int du) {
+    const int want = du <= 1024 ? 4 * du : 2 * du;
+    int lc = 6;
+    while ((1 << lc) < want) ++lc;
+    return lc;
+}
+
+// Slot of w in the table, or -1.
+__device__ __forceinline__ int table_find(const int32_t* keys, int log_cap, int32_t w) {
+    const uint32_t mask = (1u << log_cap) - 1;
+    uint32_t h = slot_of(w, log_cap);
+    int32_t k = keys[h];
+    while (k != w) {
+        if (k == -1) return -1;
+        h = (h + 1) & mask;
+        k = keys[h];
+    }
+    return (int)h;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(RX_THREADS) k_rows(
     const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
@@ -64,8 +86,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
         const int64_t a0 = upper[u];
         const int du = (int)(rowptr[u + 1] - a0);
         if (du < 2) continue;
-        int log_cap = 6;
-        while ((1 << log_cap) < 2 * du) ++log_cap;
+        const int log_cap = table_log_cap(du);
         const int cap = 1 << log_cap;
         for (int i = threadIdx.x; i < cap; i += RX_THREADS) keys[i] = -1;
         if (MODE == SUPPORT)
@@ -85,42 +106,45 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
             const int64_t b0 = upper[v], b1 = rowptr[v + 1];
             const int32_t e_uv = MODE == COUNT ? 0 : eid[a0 + j];
             uint32_t c = 0;
-            for (int64_t cb = b0; cb < b1; cb += 32) {
-                const int64_t p = cb + lane;
-                const int32_t w = p < b1 ? col[p] : INT_MAX;
+            // one hit: credit the triangle (u, v, w) found at N+(v) position p,
+            // table slot h
+            auto hit = [&](int h, int64_t p) {
+                ++c;
+                if (MODE == SUPPORT) {
+                    atomicAdd(&cnt[pos[h]], 1);
+                    atomicAdd(&sup[eid[p]], 1);
+                }
+            };
+            // the triangles of a chunk share edge (u, v): one append for all
+            auto lists = [&](int h, int64_t p) {
+                const unsigned msk = __ballot_sync(0xffffffffu, h >= 0);
+                if (!msk) return;
+                const int ldr = __ffs(msk) - 1;
+                unsigned base = 0;
+                if (lane == ldr) base = atomicAdd(&cursor[e_uv], (unsigned)__popc(msk));
+                base = __shfl_sync(0xffffffffu, base, ldr);
+                if (h >= 0) {
+                    const int32_t e_uw = eid[a0 + pos[h]], e_vw = eid[p];
+                    pairs[base + __popc(msk & lanemask_lt())] = make_int2(e_uw, e_vw);
+                    pairs[atomicAdd(&cursor[e_uw], 1u)] = make_int2(e_uv, e_vw);
+                    pairs[atomicAdd(&cursor[e_vw], 1u)] = make_int2(e_uv, e_uw);
+                }
+            };
+            // two 32-wide chunks per pass: both loads are in flight before probing
+            for (int64_t cb = b0; cb < b1; cb += 64) {
+                const int64_t p0 = cb + lane, p1 = p0 + 32;
+                const int32_t w0 = p0 < b1 ? col[p0] : INT_MAX;
+                const int32_t w1 = p1 < b1 ? col[p1] : INT_MAX;
                 // rows ascend: once a chunk starts above max N+(u), nothing later matches
-                if (__shfl_sync(0xffffffffu, w, 0) > umax) break;
-                bool hit = false;
-                uint32_t h = 0;
-                if (w <= umax) {
-                    h = slot_of(w, log_cap);
-                    int32_t kk;
-                    while ((kk = keys[h]) != -1 && kk != w) h = (h + 1) & (cap - 1);
-                    hit = kk == w;
-                }
+                if (__shfl_sync(0xffffffffu, w0, 0) > umax) break;
+                const int h0 = w0 <= umax ? table_find(keys, log_cap, w0) : -1;
+                const int h1 = w1 <= umax ? table_find(keys, log_cap, w1) : -1;
                 if (MODE == LISTS) {
-                    // the triangles of this chunk share edge (u, v): one append for all
-                    const unsigned msk = __ballot_sync(0xffffffffu, hit);
-                    if (msk) {
-                        const int ldr = __ffs(msk) - 1;
-                        unsigned base = 0;
-                        if (lane == ldr) base = atomicAdd(&cursor[e_uv], (unsigned)__popc(msk));
-                        base = __shfl_sync(0xffffffffu, base, ldr);
-                        if (hit) {
-                            const int32_t e_uw = eid[a0 + pos[h]], e_vw = eid[p];
-                            pairs[base + __popc(msk & lanemask_lt())] = make_int2(e_uw, e_vw);
-                            pairs[atomicAdd(&cursor[e_uw], 1u)] = make_int2(e_uv, e_vw);
-                            pairs[atomicAdd(&cursor[e_vw], 1u)] = make_int2(e_uv, e_uw);
-                        }
-                    }
+                    lists(h0, p0);
+                    lists(h1, p1);
                 }
-                if (hit) {
-                    ++c;
-                    if (MODE == SUPPORT) {
-                        atomicAdd(&cnt[pos[h]], 1);
-                        atomicAdd(&sup[eid[p]], 1);
-                    }
-                }
+                if (h0 >= 0) hit(h0, p0);
+                if (h1 >= 0) hit(h1, p1);
             }
             c = warp_sum(c);
             if (lane == 0) {
@@ -329,11 +353,7 @@ __global__ void k_u32_from_u64(const unsigned long long* __restrict__ in, int64_
         out[i] = (unsigned int)in[i];
 }
 
-int rows_log_cap(const Graph* g) {
-    int lc = 6;
-    while ((1 << lc) < 2 * g->max_out) ++lc;
-    return lc;
-}
+int rows_log_cap(const Graph* g) { return table_log_cap(g->max_out); }
 
 size_t rows_smem(int log_cap, int mode) {
     const size_t cap = (size_t)1 << log_cap;
@@ -350,9 +370,7 @@ int ensure_rows_smem_limit() {
     TC_CUDA_TRY(cudaGetDevice(&dev));
     const unsigned long long bit = 1ull << (dev & 63);
     if (done.load() & bit) return TC_OK;
-    int lc = 6;
-    while ((1 << lc) < 2 * RX_MAX_OUT) ++lc;
-    const int sm_max = (int)rows_smem(lc, SUPPORT);
+    const int sm_max = (int)rows_smem(table_log_cap(RX_MAX_OUT), SUPPORT);
     TC_CUDA_TRY(cudaFuncSetAttribute(k_rows<COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_max));
     TC_CUDA_TRY(cudaFuncSetAttribute(k_rows<SUPPORT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_max));
     TC_CUDA_TRY(cudaFuncSetAttribute(k_rows<LISTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_max));
