@@ -26,7 +26,19 @@
 namespace tc {
 namespace {
 
-constexpr int RX_THREADS = 256;
+#ifndef TC_RX_THREADS
+#define TC_RX_THREADS 256
+#endif
+#ifndef TC_RX_UNROLL
+#define TC_RX_UNROLL 4     // 32-wide chunks of N+(v) in flight per warp pass
+#endif
+#ifndef TC_RX_SPARSE_LIMIT
+#define TC_RX_SPARSE_LIMIT 1024  // rows up to this size get the sparser table
+#endif
+#ifndef TC_RX_SPARSE_FACTOR
+#define TC_RX_SPARSE_FACTOR 4    // table slots per entry for those rows
+#endif
+constexpr int RX_THREADS = TC_RX_THREADS;
 constexpr int RX_WARPS = RX_THREADS / 32;
 constexpr int RX_MAX_OUT = 8192;  // largest |N+(u)| the shared table holds (load <= 1/2)
 constexpr int IX_THREADS = 256;
@@ -40,7 +52,7 @@ __device__ __forceinline__ uint32_t slot_of(int32_t w, int log_cap) {
 // Table size for an out-list of du entries: load <= 1/4 up to 1024 entries
 // (short probe runs: a warp waits for its slowest lane), <= 1/2 above.
 __host__ __device__ __forceinline__ int table_log_cap(int du) {
-    const int want = du <= 1024 ? 4 * du : 2 * du;
+    const int want = du <= TC_RX_SPARSE_LIMIT ? TC_RX_SPARSE_FACTOR * du : 2 * du;
     int lc = 6;
     while ((1 << lc) < want) ++lc;
     return lc;
@@ -86,7 +98,9 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
         const int64_t a0 = upper[u];
         const int du = (int)(rowptr[u + 1] - a0);
         if (du < 2) continue;
-        const int log_cap = table_log_cap(du);
+        // clamped to the block's table (never binding when sized as the host
+        // sizes it; a clamped table still has load <= 1/2 since du <= max_out)
+        const int log_cap = min(table_log_cap(du), max_log_cap);
         const int cap = 1 << log_cap;
         for (int i = threadIdx.x; i < cap; i += RX_THREADS) keys[i] = -1;
         if (MODE == SUPPORT)
@@ -130,21 +144,27 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
                     pairs[atomicAdd(&cursor[e_vw], 1u)] = make_int2(e_uv, e_uw);
                 }
             };
-            // two 32-wide chunks per pass: both loads are in flight before probing
-            for (int64_t cb = b0; cb < b1; cb += 64) {
-                const int64_t p0 = cb + lane, p1 = p0 + 32;
-                const int32_t w0 = p0 < b1 ? col[p0] : INT_MAX;
-                const int32_t w1 = p1 < b1 ? col[p1] : INT_MAX;
-                // rows ascend: once a chunk starts above max N+(u), nothing later matches
-                if (__shfl_sync(0xffffffffu, w0, 0) > umax) break;
-                const int h0 = w0 <= umax ? table_find(keys, log_cap, w0) : -1;
-                const int h1 = w1 <= umax ? table_find(keys, log_cap, w1) : -1;
-                if (MODE == LISTS) {
-                    lists(h0, p0);
-                    lists(h1, p1);
+            // TC_RX_UNROLL 32-wide chunks per pass: their loads are in flight
+            // before any probe
+            for (int64_t cb = b0; cb < b1; cb += 32 * TC_RX_UNROLL) {
+                int32_t w[TC_RX_UNROLL];
+#pragma unroll
+                for (int q = 0; q < TC_RX_UNROLL; ++q) {
+                    const int64_t p = cb + 32 * q + lane;
+                    w[q] = p < b1 ? col[p] : INT_MAX;
                 }
-                if (h0 >= 0) hit(h0, p0);
-                if (h1 >= 0) hit(h1, p1);
+                // rows ascend: once a chunk starts above max N+(u), nothing later matches
+                if (__shfl_sync(0xffffffffu, w[0], 0) > umax) break;
+                int h[TC_RX_UNROLL];
+#pragma unroll
+                for (int q = 0; q < TC_RX_UNROLL; ++q)
+                    h[q] = w[q] <= umax ? table_find(keys, log_cap, w[q]) : -1;
+#pragma unroll
+                for (int q = 0; q < TC_RX_UNROLL; ++q) {
+                    const int64_t p = cb + 32 * q + lane;
+                    if (MODE == LISTS) lists(h[q], p);
+                    if (h[q] >= 0) hit(h[q], p);
+                }
             }
             c = warp_sum(c);
             if (lane == 0) {
@@ -353,7 +373,15 @@ __global__ void k_u32_from_u64(const unsigned long long* __restrict__ in, int64_
         out[i] = (unsigned int)in[i];
 }
 
-int rows_log_cap(const Graph* g) { return table_log_cap(g->max_out); }
+// The block's table must hold the largest table any row up to max_out
+// entries asks for; table_log_cap is not monotone across the sparse limit,
+// so take both regimes' largest.
+int max_table_log_cap(int max_out) {
+    return std::max(table_log_cap(std::min(max_out, (int)TC_RX_SPARSE_LIMIT)),
+                    table_log_cap(max_out));
+}
+
+int rows_log_cap(const Graph* g) { return max_table_log_cap(g->max_out); }
 
 size_t rows_smem(int log_cap, int mode) {
     const size_t cap = (size_t)1 << log_cap;
@@ -370,7 +398,7 @@ int ensure_rows_smem_limit() {
     TC_CUDA_TRY(cudaGetDevice(&dev));
     const unsigned long long bit = 1ull << (dev & 63);
     if (done.load() & bit) return TC_OK;
-    const int sm_max = (int)rows_smem(table_log_cap(RX_MAX_OUT), SUPPORT);
+    const int sm_max = (int)rows_smem(max_table_log_cap(RX_MAX_OUT), SUPPORT);
     TC_CUDA_TRY(cudaFuncSetAttribute(k_rows<COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_max));
     TC_CUDA_TRY(cudaFuncSetAttribute(k_rows<SUPPORT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_max));
     TC_CUDA_TRY(cudaFuncSetAttribute(k_rows<LISTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_max));

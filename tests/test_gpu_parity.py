@@ -318,3 +318,21 @@ def test_bounded_wait_expiry_is_reported():
     assert np.array_equal(truss.cpu().numpy(), og.truss_decomposition()[1])
     assert tc.tc_graph_info(g)["peel_rounds"] > 0
     g.free()
+
+
+def test_dense_graph_with_large_out_lists():
+    """K_2100: all degrees tie, so out-lists take every size 0..2099 (both
+    hash-table regimes, and a table above 48 KB of shared memory); count and
+    supports against the closed forms C(n,3) and n-2, and the n-truss."""
+    import math
+    n = 2100
+    s, d, _ = graphgen.complete(n)
+    g = tc.tc_build_csr(dev(s), dev(d), n)
+    assert tc.tc_graph_info(g)["max_out"] == n - 1
+    assert tc.tc_count(g) == math.comb(n, 3)
+    sup, T = tc.tc_edge_support(g)
+    assert T == math.comb(n, 3)
+    assert bool((sup == n - 2).all())
+    mask, left = tc.ktruss(g, n)
+    assert left == g.m and bool((mask == 1).all())
+    g.free()
