@@ -175,6 +175,13 @@ typedef struct {
                               level-scan entry, 8 per triangle- or neighbour-list
                               entry read, 4 per binary-search step and per edge
                               state read, 8 per support decrement */
+    /* that peel's work: level-scan entries, list entries read, binary-search
+     * steps, edge-state reads, support decrements */
+    int64_t peel_scanned;
+    int64_t peel_entries;
+    int64_t peel_searches;
+    int64_t peel_lookups;
+    int64_t peel_lowered;
 } tc_graph_info_t;
 
 /* Fills *info (host pointer) from values the library already holds; launches
@@ -184,6 +191,17 @@ int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream);
 /* Computes (once per graph, one kernel) the sum over oriented edges (u, v)
  * of |N+(u)| + |N+(v)| into *out (host).  Synchronises the stream. */
 int tc_graph_wedge_work(tc_graph* g, int64_t* out, void* cuda_stream);
+
+/*
+ * Bounds the optional device memory the library may use for this graph
+ * beyond its CSR, edge arrays and call scratch: the per-edge triangle lists
+ * of the peel (24 bytes per triangle, used only when they fit), their cache,
+ * and the cached compacted adjacency of the latest ktruss.  bytes < 0 (the
+ * default): a share of the device's free memory at each call.  Results do
+ * not depend on it; memory use and speed do.  A serving loop sets it to keep
+ * many resident graphs within a device-memory budget.
+ */
+int tc_graph_set_memory_limit(tc_graph* g, int64_t bytes);
 
 /* Number of CUDA kernels the library has launched in this process (all
  * graphs, all threads); lets a caller count the launches of a region. */

@@ -30,6 +30,7 @@ __all__ = [
     "TCError", "Graph", "load_library", "library_path", "tc_build_csr", "tc_count",
     "tc_edge_support", "ktruss", "ktruss_max", "tc_num_edges", "tc_num_vertices", "tc_edges",
     "tc_graph_info", "tc_graph_wedge_work", "tc_launch_count", "tc_batch_run",
+    "tc_graph_set_memory_limit",
     "tc_graph_free", "tc_strerror", "tc_last_error", "tc_debug_fail_alloc",
     "tc_debug_spin_limit_ns", "tc_debug_peel_mode", "tc_debug_intersect_mode", "TC_OK", "TC_EINVAL", "TC_ERANGE", "TC_ENOMEM", "TC_ECUDA",
     "TC_ETIMEDOUT", "TC_EOVERFLOW", "TC_INPUT_AUTO", "TC_INPUT_DEVICE", "TC_INPUT_HOST",
@@ -73,6 +74,7 @@ def load_library(build_if_missing: bool = True):
             "tc_last_error": (ctypes.c_char_p, []),
             "tc_graph_info": (ctypes.c_int, [vp, ctypes.POINTER(GraphInfo), vp]),
             "tc_launch_count": (i64, []),
+            "tc_graph_set_memory_limit": (ctypes.c_int, [vp, i64]),
             "tc_batch_run": (ctypes.c_int, [ctypes.POINTER(BatchDesc), vp]),
             "tc_graph_wedge_work": (ctypes.c_int, [vp, ctypes.POINTER(i64), vp]),
             "tc_debug_fail_alloc": (i64, [i64]),
@@ -93,7 +95,8 @@ class GraphInfo(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in
                 ("n", "m_in", "m", "max_degree", "max_out", "wedge_work", "device_bytes",
                  "peel_rounds", "peel_lists", "count_kernel_ns", "support_kernel_ns",
-                 "lists_kernel_ns", "peel_kernel_ns", "peel_bytes")]
+                 "lists_kernel_ns", "peel_kernel_ns", "peel_bytes", "peel_scanned",
+                 "peel_entries", "peel_searches", "peel_lookups", "peel_lowered")]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -311,6 +314,12 @@ def tc_graph_wedge_work(g: Graph, stream=None) -> int:
     _check(load_library().tc_graph_wedge_work(g.handle, ctypes.byref(out), _stream_handle(stream)),
            "tc_graph_wedge_work")
     return out.value
+
+
+def tc_graph_set_memory_limit(g: Graph, nbytes: int):
+    """Bound on the optional device memory (triangle lists, caches) for this graph; <0 = auto."""
+    _check(load_library().tc_graph_set_memory_limit(g.handle, int(nbytes)),
+           "tc_graph_set_memory_limit")
 
 
 def tc_launch_count() -> int:

@@ -30,7 +30,7 @@ namespace {
 #define TC_RX_THREADS 256
 #endif
 #ifndef TC_RX_UNROLL
-#define TC_RX_UNROLL 4     // 32-wide chunks of N+(v) in flight per warp pass
+#define TC_RX_UNROLL 8     // 32-wide chunks of N+(v) in flight per warp pass
 #endif
 #ifndef TC_RX_SPARSE_LIMIT
 #define TC_RX_SPARSE_LIMIT 1024  // rows up to this size get the sparser table

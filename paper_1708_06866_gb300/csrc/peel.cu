@@ -31,7 +31,10 @@
 namespace tc {
 namespace {
 
-constexpr int PK_THREADS = 512;
+#ifndef TC_PK_THREADS
+#define TC_PK_THREADS 1024
+#endif
+constexpr int PK_THREADS = TC_PK_THREADS;
 constexpr int PK_WARPS = PK_THREADS / 32;
 constexpr int WINDOW = 8;        // support values one full scan covers (see k_peel)
 constexpr int64_t HEAVY = 4096;  // triangle-list length above which an edge is "heavy"
@@ -587,12 +590,24 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
     const int forced = form != PEEL_AUTO ? form : peel_mode();
     p.tl = false;
     // list positions are 32-bit: the triangle-list form needs 3T < 2^32
+    size_t free_b = 0, total_b = 0;
+    TC_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    // optional memory (lists, caches) stays within the graph's limit, or a
+    // share of the free memory when the caller set none
+    const double allowance =
+        g->mem_limit >= 0 ? (double)g->mem_limit : 0.6 * (double)free_b;
     if (triangle_lists_supported(g) && forced != PEEL_INTERSECT &&
         3 * g->triangles < 0xffffffffLL) {
         const double need = 24.0 * (double)g->triangles + 16.0 * (double)(m + 1);
-        size_t free_b = 0, total_b = 0;
-        TC_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-        p.tl = forced == PEEL_LISTS || need < 0.6 * (double)free_b;
+        p.tl = forced == PEEL_LISTS || need <= allowance ||
+               (g->tri_valid && g->mem_limit < 0);
+    }
+    if (!p.tl && g->tri_off) {  // cached lists above a lowered limit are dropped
+        dev_free(g->tri_off, g->last_stream);
+        dev_free(g->tri_pairs, g->last_stream);
+        g->tri_off = nullptr;
+        g->tri_pairs = nullptr;
+        g->tri_valid = false;
     }
     if (p.tl && g->tri_valid) {
         p.off = g->tri_off;  // built by an earlier peel of this graph
@@ -620,9 +635,18 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
     } else if (p.cache) {
         // the compacted adjacency stays with the graph when it fits
         p.fresh_adj = !(p.resume && g->kt_adj);
-        size_t free_b = 0, total_b = 0;
-        TC_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-        const bool room = g->kt_col || (double)(16 * m + 4 * (int64_t)g->n) < 0.4 * (double)free_b;
+        const double adj_bytes = (double)(16 * m + 4 * (int64_t)g->n);
+        if (g->kt_col && g->mem_limit >= 0 && adj_bytes > (double)g->mem_limit) {
+            dev_free(g->kt_col, g->last_stream);  // above a lowered limit
+            dev_free(g->kt_eid, g->last_stream);
+            dev_free(g->kt_rowlen, g->last_stream);
+            g->kt_col = g->kt_eid = nullptr;
+            g->kt_rowlen = nullptr;
+            g->kt_adj = false;
+            p.fresh_adj = true;
+        }
+        const bool room = g->kt_col || (g->mem_limit >= 0 ? adj_bytes <= (double)g->mem_limit
+                                                          : adj_bytes < 0.4 * (double)free_b);
         if (room) {
             if (!g->kt_col) {
                 TC_TRY(dev_alloc_n(&g->kt_col, 2 * m, g->last_stream));
@@ -665,7 +689,7 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
     // small graphs get a smaller grid (cheaper barriers, and room for other
     // streams' work); large ones fill every SM twice
     const int64_t want = std::max<int64_t>(1, (m + 8191) / 8192);
-    p.blocks = (int)std::min<int64_t>(want, (int64_t)num_sms() * std::min(per_sm, 2));
+    p.blocks = (int)std::min<int64_t>(want, (int64_t)num_sms() * std::min(per_sm, 1024 / PK_THREADS));
     g->last_peel_lists = p.tl;
     return TC_OK;
 }
@@ -727,6 +751,11 @@ int peel_finish(PeelPlan* pp, cudaStream_t s, int64_t* n_alive, int32_t* kmax) {
     // (12 B); a triangle-list entry is an 8-B pair, a neighbour-list entry
     // an id and an edge id (8 B); binary-search steps and state lookups read
     // 4 B each; a decrement is a 4-B read-modify-write (8 B)
+    g->stats.peel_scanned = (int64_t)r.scanned;
+    g->stats.peel_entries = (int64_t)r.entries;
+    g->stats.peel_searches = (int64_t)r.searches;
+    g->stats.peel_lookups = (int64_t)r.lookups;
+    g->stats.peel_lowered = (int64_t)r.lowered;
     g->stats.peel_bytes = 12 * (int64_t)r.scanned + 8 * (int64_t)r.entries +
                           4 * (int64_t)r.searches + 4 * (int64_t)r.lookups +
                           8 * (int64_t)r.lowered;

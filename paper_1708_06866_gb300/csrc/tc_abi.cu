@@ -331,6 +331,11 @@ int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream) {
     info->lists_kernel_ns = gg->stats.lists_ns;
     info->peel_kernel_ns = gg->stats.peel_ns;
     info->peel_bytes = gg->stats.peel_bytes;
+    info->peel_scanned = gg->stats.peel_scanned;
+    info->peel_entries = gg->stats.peel_entries;
+    info->peel_searches = gg->stats.peel_searches;
+    info->peel_lookups = gg->stats.peel_lookups;
+    info->peel_lowered = gg->stats.peel_lowered;
     return TC_OK;
 }
 
@@ -339,6 +344,12 @@ int tc_graph_wedge_work(tc_graph* g, int64_t* out, void* cuda_stream) {
     if (!out) return fail(TC_EINVAL, "out is NULL");
     DeviceGuard dg(g->g.device);
     return tc::graph_wedge_work(&g->g, out, as_stream(cuda_stream));
+}
+
+int tc_graph_set_memory_limit(tc_graph* g, int64_t bytes) {
+    if (!g) return fail(TC_EINVAL, "graph is NULL");
+    g->g.mem_limit = bytes < 0 ? -1 : bytes;
+    return TC_OK;
 }
 
 int64_t tc_launch_count(void) { return tc::g_launches.load(); }

@@ -236,6 +236,8 @@ struct Graph {
     struct {
         int64_t count_ns = -1, support_ns = -1, lists_ns = -1, peel_ns = -1;
         int64_t peel_bytes = -1;
+        int64_t peel_scanned = 0, peel_entries = 0, peel_searches = 0, peel_lookups = 0,
+                peel_lowered = 0;
     } stats;  // device time of the latest launch of each main kernel
     // cached support (internal order) and triangle count
     int32_t* support = nullptr;
@@ -256,6 +258,9 @@ struct Graph {
     int32_t* kt_eid = nullptr;
     int32_t* kt_rowlen = nullptr;
     bool kt_adj = false;
+    // bound on optional device memory for this graph (triangle lists, their
+    // cache, the cached compacted adjacency); -1 = a share of free memory
+    int64_t mem_limit = -1;
     int64_t triangles = -1;
     int* dev_err = nullptr;
     unsigned long long* dev_scalars = nullptr;  // small device scratch (8 words)

@@ -61,16 +61,22 @@ class GpuBackend:
     def new_stream(self):
         return self.torch.cuda.Stream(device=self.device)
 
+    # per input pair: CSR and edge arrays (~40 B), call scratch of a peel
+    # (~60 B), and the optional memory (triangle lists, caches) the graph may
+    # use (OPTIONAL_PER_PAIR, enforced through tc_graph_set_memory_limit)
+    OPTIONAL_PER_PAIR = 40
+
     def estimate_bytes(self, gid: int) -> int:
-        """Device bytes a graph needs while it is used: the CSR and edge arrays
-        (~40 B per input pair) plus query scratch (~60 B per input pair)."""
+        """Device bytes a graph may need while it is used."""
         src, _, _ = self.graphs[gid]
-        return 100 * len(src) + (1 << 20)
+        return (100 + self.OPTIONAL_PER_PAIR) * len(src) + (1 << 20)
 
     def build(self, gid: int, stream):
         src, dst, n = self.graphs[gid]
         with self.torch.cuda.stream(stream):
-            return self.tc.tc_build_csr(src, dst, n, stream=stream)
+            g = self.tc.tc_build_csr(src, dst, n, stream=stream)
+        self.tc.tc_graph_set_memory_limit(g, self.OPTIONAL_PER_PAIR * len(src))
+        return g
 
     def free(self, handle):
         handle.free()

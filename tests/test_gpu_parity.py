@@ -336,3 +336,35 @@ def test_dense_graph_with_large_out_lists():
     mask, left = tc.ktruss(g, n)
     assert left == g.m and bool((mask == 1).all())
     g.free()
+
+
+def test_memory_limit_selects_the_peel_form_and_keeps_results():
+    """tc_graph_set_memory_limit bounds the optional memory: with 0 the peel
+    runs without triangle lists or cached adjacency; a generous limit lets it
+    keep lists; lowering the limit drops what is cached.  Results do not
+    change."""
+    src, dst, n = graphgen.rmat(12, 16, seed=21)
+    og = oracle.OracleGraph.from_edges(src, dst, n)
+    ref = {k: og.ktruss(k) for k in (3, 5)}
+    g = tc.tc_build_csr(dev(src), dev(dst), n)
+    base = tc.tc_graph_info(g)["device_bytes"]
+    tc.tc_graph_set_memory_limit(g, 1 << 40)
+    for k in (3, 5):
+        mk, c = tc.ktruss(g, k)
+        assert c == ref[k][2] and np.array_equal(mk.cpu().numpy(), ref[k][0])
+    info = tc.tc_graph_info(g)
+    assert info["peel_lists"] == 1
+    held = info["device_bytes"]
+    assert held > base
+    tc.tc_graph_set_memory_limit(g, 0)
+    for k in (3, 5):
+        mk, c = tc.ktruss(g, k)
+        assert c == ref[k][2] and np.array_equal(mk.cpu().numpy(), ref[k][0])
+    info = tc.tc_graph_info(g)
+    assert info["peel_lists"] == 0
+    assert info["device_bytes"] < held
+    kmax, truss = tc.ktruss_max(g)
+    want_kmax, want_truss = og.truss_decomposition()
+    assert kmax == want_kmax and np.array_equal(truss.cpu().numpy(), want_truss)
+    assert tc.load_library().tc_graph_set_memory_limit(None, 0) == tc.TC_EINVAL
+    tc.tc_graph_free(g)
