@@ -15,6 +15,11 @@
 // N+(u) at a time and its lanes stream N+(v) with coalesced loads, probing
 // the table for every w.  A third mode writes each edge's triangle list (the
 // ids of the two other edges of every triangle through it) for the peel.
+// Each edge's list fills from both ends: triangles found in the edge's own
+// source row (where the edge is (u, v) or (u, w) of a triangle u < v < w)
+// from the bottom through shared-memory cursors of that row, so those writes
+// stay within one block's lifetime; the rest (the edge is (v, w)) from the
+// top through one global cursor per edge.
 // Graphs whose largest out-list exceeds the table capacity use k_edges_warp
 // (one warp per oriented edge, binary search in global memory).
 #include <algorithm>
@@ -75,14 +80,19 @@ template <int MODE>
 __global__ void __launch_bounds__(RX_THREADS) k_rows(
     const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
     const int32_t* __restrict__ col, const int32_t* __restrict__ eid, int32_t n,
-    int32_t* __restrict__ sup, unsigned int* __restrict__ cursor,
-    int2* __restrict__ pairs, unsigned int* __restrict__ next_row,
-    unsigned long long* __restrict__ partials, int max_log_cap) {
+    int32_t* __restrict__ sup, const unsigned long long* __restrict__ off,
+    unsigned int* __restrict__ top, int2* __restrict__ pairs, unsigned int* __restrict__ next_row,
+    unsigned long long* __restrict__ partials, int max_log_cap, int max_pos) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int max_cap = 1 << max_log_cap;
     int32_t* keys = reinterpret_cast<int32_t*>(smem);
     uint16_t* pos = reinterpret_cast<uint16_t*>(keys + max_cap);
-    int32_t* cnt = reinterpret_cast<int32_t*>(pos + max_cap);  // SUPPORT: per position of N+(u)
+    // per position i of N+(u): SUPPORT: triangles credited to (u, N+(u)[i]);
+    // LISTS: entries written at the bottom of that edge's list, the list's
+    // start and the edge id
+    int32_t* cnt = reinterpret_cast<int32_t*>(pos + max_cap);
+    unsigned int* sbase = reinterpret_cast<unsigned int*>(cnt + max_pos);
+    int32_t* seid = reinterpret_cast<int32_t*>(sbase + max_pos);
     __shared__ int s_row;
     __shared__ unsigned long long s_acc[RX_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -105,6 +115,13 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
         for (int i = threadIdx.x; i < cap; i += RX_THREADS) keys[i] = -1;
         if (MODE == SUPPORT)
             for (int i = threadIdx.x; i < du; i += RX_THREADS) cnt[i] = 0;
+        if (MODE == LISTS)
+            for (int i = threadIdx.x; i < du; i += RX_THREADS) {
+                const int32_t e = eid[a0 + i];
+                cnt[i] = 0;
+                seid[i] = e;
+                sbase[i] = (unsigned int)off[e];
+            }
         __syncthreads();
         for (int i = threadIdx.x; i < du; i += RX_THREADS) {
             const int32_t w = col[a0 + i];
@@ -118,7 +135,8 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
         for (int j = warp; j < du - 1; j += RX_WARPS) {
             const int32_t v = col[a0 + j];
             const int64_t b0 = upper[v], b1 = rowptr[v + 1];
-            const int32_t e_uv = MODE == COUNT ? 0 : eid[a0 + j];
+            const int32_t e_uv = MODE == COUNT ? 0 : MODE == LISTS ? seid[j] : eid[a0 + j];
+            const unsigned int base_uv = MODE == LISTS ? sbase[j] : 0u;
             uint32_t c = 0;
             // one hit: credit the triangle (u, v, w) found at N+(v) position p,
             // table slot h
@@ -129,19 +147,23 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
                     atomicAdd(&sup[eid[p]], 1);
                 }
             };
-            // the triangles of a chunk share edge (u, v): one append for all
+            // the triangles of a chunk share edge (u, v): one append for all;
+            // (u, v) and (u, w) fill from the bottom (this row's cursors),
+            // (v, w) from the top
             auto lists = [&](int h, int64_t p) {
                 const unsigned msk = __ballot_sync(0xffffffffu, h >= 0);
                 if (!msk) return;
                 const int ldr = __ffs(msk) - 1;
                 unsigned base = 0;
-                if (lane == ldr) base = atomicAdd(&cursor[e_uv], (unsigned)__popc(msk));
+                if (lane == ldr) base = atomicAdd((unsigned int*)&cnt[j], (unsigned)__popc(msk));
                 base = __shfl_sync(0xffffffffu, base, ldr);
                 if (h >= 0) {
-                    const int32_t e_uw = eid[a0 + pos[h]], e_vw = eid[p];
-                    pairs[base + __popc(msk & lanemask_lt())] = make_int2(e_uw, e_vw);
-                    pairs[atomicAdd(&cursor[e_uw], 1u)] = make_int2(e_uv, e_vw);
-                    pairs[atomicAdd(&cursor[e_vw], 1u)] = make_int2(e_uv, e_uw);
+                    const int iw = pos[h];
+                    const int32_t e_uw = seid[iw], e_vw = eid[p];
+                    pairs[base_uv + base + __popc(msk & lanemask_lt())] = make_int2(e_uw, e_vw);
+                    pairs[sbase[iw] + atomicAdd((unsigned int*)&cnt[iw], 1u)] =
+                        make_int2(e_uv, e_vw);
+                    pairs[atomicSub(&top[e_vw], 1u) - 1u] = make_int2(e_uv, e_uw);
                 }
             };
             // TC_RX_UNROLL 32-wide chunks per pass: their loads are in flight
@@ -383,9 +405,12 @@ int max_table_log_cap(int max_out) {
 
 int rows_log_cap(const Graph* g) { return max_table_log_cap(g->max_out); }
 
-size_t rows_smem(int log_cap, int mode) {
+// Table (keys + positions) and the per-position arrays of SUPPORT (4 B) and
+// LISTS (12 B) for out-lists of up to max_pos entries.
+size_t rows_smem(int log_cap, int mode, int max_pos) {
     const size_t cap = (size_t)1 << log_cap;
-    return cap * 4 + cap * 2 + (mode == SUPPORT ? (cap / 2) * 4 : 0) + 16;
+    const size_t per = mode == SUPPORT ? 4 : mode == LISTS ? 12 : 0;
+    return cap * 4 + cap * 2 + per * (size_t)std::max(max_pos, 1) + 16;
 }
 
 // The row kernel's dynamic shared memory depends on the graph.  The
@@ -398,7 +423,7 @@ int ensure_rows_smem_limit() {
     TC_CUDA_TRY(cudaGetDevice(&dev));
     const unsigned long long bit = 1ull << (dev & 63);
     if (done.load() & bit) return TC_OK;
-    const int sm_max = (int)rows_smem(max_table_log_cap(RX_MAX_OUT), SUPPORT);
+    const int sm_max = (int)rows_smem(max_table_log_cap(RX_MAX_OUT), LISTS, RX_MAX_OUT);
     TC_CUDA_TRY(cudaFuncSetAttribute(k_rows<COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_max));
     TC_CUDA_TRY(cudaFuncSetAttribute(k_rows<SUPPORT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_max));
     TC_CUDA_TRY(cudaFuncSetAttribute(k_rows<LISTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_max));
@@ -407,22 +432,25 @@ int ensure_rows_smem_limit() {
 }
 
 template <int MODE>
-int launch_rows(Graph* g, int32_t* sup, unsigned int* cursor, int2* pairs,
-                unsigned long long* partials, int blocks, cudaStream_t s) {
+int launch_rows(Graph* g, int32_t* sup, const unsigned long long* off, unsigned int* top,
+                int2* pairs, unsigned long long* partials, int blocks, cudaStream_t s) {
     TC_TRY(ensure_rows_smem_limit());
+    if (g->max_out > RX_MAX_OUT) return fail(TC_EINVAL, "internal: row kernel above its table size");
     const int lc = rows_log_cap(g);
-    const size_t sm = rows_smem(lc, MODE);
+    const int max_pos = std::max(g->max_out, 1);
+    const size_t sm = rows_smem(lc, MODE, max_pos);
     unsigned int* next_row = reinterpret_cast<unsigned int*>(g->dev_scalars + 4);
     TC_CUDA_TRY(cudaMemsetAsync(next_row, 0, sizeof(unsigned int), s));
     k_rows<MODE><<<blocks, RX_THREADS, sm, s>>>(g->rowptr, g->upper, g->col, g->eid, g->n, sup,
-                                                cursor, pairs, next_row, partials, lc);
+                                                off, top, pairs, next_row, partials, lc,
+                                                max_pos);
     TC_LAUNCH_CHECK("k_rows");
     return TC_OK;
 }
 
 int rows_blocks(Graph* g, int mode) {
     int per_sm = 0;
-    const size_t sm = rows_smem(rows_log_cap(g), mode);
+    const size_t sm = rows_smem(rows_log_cap(g), mode, std::max(g->max_out, 1));
     cudaError_t e = cudaSuccess;
     if (ensure_rows_smem_limit() != TC_OK) per_sm = 1;
     else if (mode == COUNT)
@@ -475,8 +503,8 @@ int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangle
     TC_TRY(timer.start(s));
     if (rows) {
         if (want_support)
-            TC_TRY(launch_rows<SUPPORT>(g, sup, nullptr, nullptr, partials, blocks, s));
-        else TC_TRY(launch_rows<COUNT>(g, nullptr, nullptr, nullptr, partials, blocks, s));
+            TC_TRY(launch_rows<SUPPORT>(g, sup, nullptr, nullptr, nullptr, partials, blocks, s));
+        else TC_TRY(launch_rows<COUNT>(g, nullptr, nullptr, nullptr, nullptr, partials, blocks, s));
     } else if (want_support) {
         k_edges_warp<true><<<blocks, IX_THREADS, 0, s>>>(g->ends, g->rowptr, g->upper,
                                                          g->col, g->eid, m, sup, partials);
@@ -523,7 +551,7 @@ int plan_triangle_lists(Graph* g, Scratch& sc, ListsPlan* lp) {
     const int64_t m = g->m;
     lp->chunks = (m + SC_CHUNK - 1) / SC_CHUNK;
     TC_TRY(sc.alloc(&lp->sums, lp->chunks));
-    TC_TRY(sc.alloc(&lp->cursor, m));
+    TC_TRY(sc.alloc(&lp->top, m));
     lp->blocks = rows_blocks(g, LISTS);
     TC_TRY(sc.alloc(&lp->partials, lp->blocks));
     return TC_OK;
@@ -531,8 +559,8 @@ int plan_triangle_lists(Graph* g, Scratch& sc, ListsPlan* lp) {
 
 // Offsets = exclusive scan of the supports; then every triangle writes its
 // pair into the lists of its three edges.  List positions fit in 32 bits
-// (the caller keeps 3T below 2^32), so a 4-byte cursor per edge keeps the
-// cursor array small enough for L2.
+// (the caller keeps 3T below 2^32), so a 4-byte top cursor per edge
+// (starting at the end of its list) keeps the cursor array small enough for L2.
 int enqueue_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off, int2* pairs,
                            ListsPlan* lp, cudaStream_t s) {
     const int64_t m = g->m;
@@ -543,10 +571,10 @@ int enqueue_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off
     k_chunk_scan<<<(unsigned)lp->chunks, SC_THREADS, 0, s>>>(sup, m, lp->sums, off);
     TC_LAUNCH_CHECK("k_chunk_scan");
     k_u32_from_u64<<<(unsigned)std::min<int64_t>((m + 255) / 256, (int64_t)num_sms() * 16), 256, 0,
-                     s>>>(off, m, lp->cursor);
+                     s>>>(off + 1, m, lp->top);
     TC_LAUNCH_CHECK("k_u32_from_u64");
     TC_TRY(lp->timer.start(s));
-    TC_TRY(launch_rows<LISTS>(g, nullptr, lp->cursor, pairs, lp->partials, lp->blocks, s));
+    TC_TRY(launch_rows<LISTS>(g, nullptr, off, lp->top, pairs, lp->partials, lp->blocks, s));
     TC_TRY(lp->timer.stop(s));
     return TC_OK;
 }

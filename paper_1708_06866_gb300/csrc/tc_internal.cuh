@@ -271,7 +271,7 @@ struct Graph {
 struct ListsPlan {
     unsigned long long* sums = nullptr;  // per-chunk sums of the offset scan
     int64_t chunks = 0;
-    unsigned int* cursor = nullptr;      // per-edge fill positions
+    unsigned int* top = nullptr;         // per-edge fill positions from the list's end
     unsigned long long* partials = nullptr;
     int blocks = 0;
     KernelTimer timer;
