@@ -285,6 +285,10 @@ WORKLOADS = {
         "rmat20", "rmat", n=1 << 20, scale=20, seed=1,
         description="R-MAT scale 20, edgefactor 16, a/b/c/d=.57/.19/.19/.05, permuted; "
                     "count + support + full truss decomposition k=3..kmax"),
+    "rmat18": Workload(
+        "rmat18", "rmat", n=1 << 18, scale=18, seed=1,
+        description="R-MAT scale 18, edgefactor 16, permuted; count + support + full truss "
+                    "decomposition (the small case for hardware-counter captures)"),
     "rmat24": Workload(
         "rmat24", "rmat", n=1 << 24, scale=24, seed=2, truss_ks=(3, 4, 6, 8),
         description="R-MAT scale 24, edgefactor 16 (268M draws), permuted; "

@@ -38,6 +38,9 @@ constexpr int PK_THREADS = TC_PK_THREADS;
 constexpr int PK_WARPS = PK_THREADS / 32;
 constexpr int WINDOW = 8;        // support values one full scan covers (see k_peel)
 constexpr int64_t HEAVY = 4096;  // triangle-list length above which an edge is "heavy"
+#ifndef TC_PK_UNROLL
+#define TC_PK_UNROLL 2               // triangle-list entries per lane in flight
+#endif
 
 struct PeelCtl {
     unsigned long long bar;      // grid-barrier arrivals (monotonic)
@@ -203,40 +206,93 @@ __device__ __forceinline__ void destroy(const PeelArgs& a, Round rd, int32_t e, 
 // edge's current support is exactly its number of live triangles (those
 // whose other two edges are not removed): support 0 means nothing to do,
 // and a single-warp group stops once it has seen them all.
+// Lowers the support of x (x >= 0) whose decrement returned old: the
+// crossing checks of lower(), split from the atomic so that a lane can have
+// several decrements in flight.
+__device__ __forceinline__ void after_lower(const PeelArgs& a, Round rd, int32_t x, int old,
+                                            const Sinks& k, bool heavy_x) {
+    if (old == k.thr) {
+        a.t[x] = -(rd.r + 1);
+        if (heavy_x) k.Hn[atomicAdd(k.cntH, 1ull) - k.baseH] = x;
+        else k.Fn[atomicAdd(k.cntF, 1ull) - k.baseF] = x;
+    }
+    if (old == k.bound) k.Wc[atomicAdd(k.cntW, 1ull) - k.baseW] = x;
+}
+
 template <bool TL>
 __device__ __forceinline__ void process_edge(const PeelArgs& a, Round rd, int32_t e,
                                              int64_t glane, int64_t gsize, const Sinks& k,
                                              Tally& tl) {
-    const int32_t live = ld_cg(a.s + e);
-    if (live <= 0) return;
     const bool one_warp = gsize == 32;
     int32_t seen = 0;  // live triangles met so far (one_warp only; warp-uniform)
     if (TL) {
+        // the list range and the support are loaded together
         const int64_t q0 = (int64_t)a.off[e], q1 = (int64_t)a.off[e + 1];
-        for (int64_t cb = q0 + (glane & ~31ll); cb < q1; cb += gsize) {
-            const int64_t q = cb + (glane & 31);
-            bool found = false;
-            if (q < q1) {
-                ++tl.entries;
-                const int2 fg = a.pairs[q];
-                const int32_t tf = ld_cg(a.t + fg.x);
-                ++tl.lookups;
-                if (!rd.removed(tf)) {
-                    const int32_t tg = ld_cg(a.t + fg.y);
-                    ++tl.lookups;
-                    if (!rd.removed(tg)) {
-                        found = true;
-                        destroy<TL>(a, rd, e, fg.x, tf, fg.y, tg, k, tl);
-                    }
+        const int32_t live = ld_cg(a.s + e);
+        if (live <= 0) return;
+        // PU entries per lane in flight: the pair loads, then both state
+        // loads of each pair, then every decrement, then their checks
+        constexpr int PU = TC_PK_UNROLL;
+        for (int64_t b = q0; b < q1; b += gsize * PU) {  // b is uniform in the group
+            int2 fg[PU];
+            bool v[PU];
+#pragma unroll
+            for (int u = 0; u < PU; ++u) {
+                const int64_t q = b + glane + (int64_t)u * gsize;
+                v[u] = q < q1;
+                fg[u] = v[u] ? a.pairs[q] : make_int2(0, 0);
+            }
+            int32_t tf[PU], tg[PU];
+#pragma unroll
+            for (int u = 0; u < PU; ++u) {
+                tf[u] = v[u] ? ld_cg(a.t + fg[u].x) : 1;
+                tg[u] = v[u] ? ld_cg(a.t + fg[u].y) : 1;
+            }
+            int32_t xf[PU], xg[PU];
+            int of[PU], og[PU];
+            int found = 0;
+#pragma unroll
+            for (int u = 0; u < PU; ++u) {
+                xf[u] = -1;
+                xg[u] = -1;
+                if (v[u]) {
+                    ++tl.entries;
+                    tl.lookups += 2;
+                }
+                if (v[u] && !rd.removed(tf[u]) && !rd.removed(tg[u])) {
+                    ++found;
+                    // the smallest dying edge of the triangle owns it
+                    const bool own = !((rd.dying(tf[u]) && fg[u].x < e) ||
+                                       (rd.dying(tg[u]) && fg[u].y < e));
+                    if (own && rd.alive(tf[u])) xf[u] = fg[u].x;
+                    if (own && rd.alive(tg[u])) xg[u] = fg[u].y;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < PU; ++u) {
+                if (xf[u] >= 0) of[u] = atomicSub(a.s + xf[u], 1);
+                if (xg[u] >= 0) og[u] = atomicSub(a.s + xg[u], 1);
+            }
+#pragma unroll
+            for (int u = 0; u < PU; ++u) {
+                if (xf[u] >= 0) {
+                    ++tl.lowered;
+                    after_lower(a, rd, xf[u], of[u], k, is_heavy<TL>(a, xf[u]));
+                }
+                if (xg[u] >= 0) {
+                    ++tl.lowered;
+                    after_lower(a, rd, xg[u], og[u], k, is_heavy<TL>(a, xg[u]));
                 }
             }
             if (one_warp) {
-                seen += __popc(__ballot_sync(0xffffffffu, found));
+                seen += __reduce_add_sync(0xffffffffu, (unsigned)found);
                 if (seen >= live) break;
             }
         }
         return;
     }
+    const int32_t live = ld_cg(a.s + e);
+    if (live <= 0) return;
     const int2 ab = a.ends[e];
     int64_t s0 = a.rowptr[ab.x], l0 = a.rowptr[ab.y];
     int32_t sl = ld_cg(a.rowlen + ab.x), ll = ld_cg(a.rowlen + ab.y);

@@ -368,3 +368,37 @@ def test_memory_limit_selects_the_peel_form_and_keeps_results():
     assert kmax == want_kmax and np.array_equal(truss.cpu().numpy(), want_truss)
     assert tc.load_library().tc_graph_set_memory_limit(None, 0) == tc.TC_EINVAL
     tc.tc_graph_free(g)
+
+
+def test_resume_across_forms():
+    """A ktruss call resumes from the cached k-truss of an earlier call with
+    a smaller k, whichever peel form made it; calls in between (a
+    decomposition, a smaller k) leave results unchanged."""
+    src, dst, n = graphgen.rmat(11, 16, seed=33)
+    og = oracle.OracleGraph.from_edges(src, dst, n)
+    want = {k: og.ktruss(k) for k in (3, 4, 5, 6)}
+    want_kmax, want_truss = og.truss_decomposition()
+    g = tc.tc_build_csr(dev(src), dev(dst), n)
+
+    def check_k(k, mode):
+        prev = tc.tc_debug_peel_mode(mode)
+        try:
+            mk, c = tc.ktruss(g, k)
+        finally:
+            tc.tc_debug_peel_mode(prev)
+        assert c == want[k][2] and np.array_equal(mk.cpu().numpy(), want[k][0]), (k, mode)
+
+    L, X = PEEL_MODES["lists"], PEEL_MODES["intersect"]
+    check_k(3, L)
+    prev = tc.tc_debug_peel_mode(L)
+    try:
+        kmax, truss = tc.ktruss_max(g)        # a decomposition in between
+    finally:
+        tc.tc_debug_peel_mode(prev)
+    assert kmax == want_kmax and np.array_equal(truss.cpu().numpy(), want_truss)
+    check_k(4, L)                             # resumes from k = 3
+    check_k(5, X)                             # intersection form from the list state
+    check_k(6, L)                             # list form from the intersection state
+    check_k(4, L)                             # smaller k: fresh
+    check_k(6, L)                             # resumes from k = 4
+    tc.tc_graph_free(g)
