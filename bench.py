@@ -486,11 +486,29 @@ def bench_e2e(args, tc, torch, src_h, dst_h, n, wl, stream):
 
 # ------------------------------------------------------------------ oracle arm
 
-def oracle_sample_step():
+def oracle_sample_name(wl):
+    if wl is not None and wl.family == "king":
+        return "the 512 x 512 image graph (same generator)"
+    if wl is not None and wl.family == "er":
+        return f"the {wl.name} workload itself"
+    return f"R-MAT scale {CPU_SAMPLE_SCALE}, same generator and parameters, seed 1"
+
+
+def oracle_sample(wl):
+    """The bounded sample of a workload the CPU oracle runs: the same
+    generator at about a million edges."""
+    if wl is not None and wl.family == "king":
+        return graphgen.king(512)
+    if wl is not None and wl.family == "er":
+        return wl.generate()
+    return graphgen.rmat(CPU_SAMPLE_SCALE, seed=1)
+
+
+def oracle_sample_step(wl=None):
     """The CPU oracle on the bounded sample: the whole path (cleaning, count,
-    supports, truss decomposition) on the same R-MAT generator at scale 16."""
+    supports, truss decomposition)."""
     import oracle
-    s, d, n = graphgen.rmat(CPU_SAMPLE_SCALE, seed=1)
+    s, d, n = oracle_sample(wl)
     t0 = time.perf_counter()
     g = oracle.OracleGraph.from_edges(s, d, n)
     g.count()
@@ -510,12 +528,11 @@ def oracle_cores():
 def cpu_baseline(wl, reps=2):
     ms, ts = 0, 0.0
     for _ in range(reps):
-        m, dt = oracle_sample_step()
+        m, dt = oracle_sample_step(wl)
         ms += m
         ts += dt
     return {"value": ms / ts, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
-            "sample": f"oracle (serial peel; count/support loops OpenMP) on R-MAT scale "
-                      f"{CPU_SAMPLE_SCALE}, same generator and parameters, seed 1, whole path "
+            "sample": f"oracle (serial peel; count/support loops OpenMP) on {oracle_sample_name(wl)}, whole path "
                       f"(cleaning + count + support + full truss decomposition), {reps} runs, "
                       f"{ts:.1f} s; the {wl.name} workload itself is larger"}
 
@@ -523,24 +540,23 @@ def cpu_baseline(wl, reps=2):
 def bench_reference(args, rank, world):
     if rank != 0:
         return None
+    wl = graphgen.WORKLOADS.get(args.workload)
     for _ in range(args.warmup):
-        oracle_sample_step()
+        oracle_sample_step(wl)
     tot_m, tot_t = 0, 0.0
     for _ in range(args.steps):
-        m, dt = oracle_sample_step()
+        m, dt = oracle_sample_step(wl)
         tot_m += m
         tot_t += dt
     value = tot_m / tot_t
-    wl = graphgen.WORKLOADS[args.workload]
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": wl.name, "sample_scale": CPU_SAMPLE_SCALE},
+            "config": {"workload": args.workload},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_cores(),
                              "kind": "oracle",
-                             "sample": f"R-MAT scale {CPU_SAMPLE_SCALE} (same generator), "
-                                       "whole path per step"},
+                             "sample": f"{oracle_sample_name(wl)}, whole path per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 

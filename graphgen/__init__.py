@@ -57,6 +57,7 @@ def _load():
                                       ctypes.c_int, i32p, i32p]
             lib.gg_er.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, i32p, i32p]
             lib.gg_permutation.argtypes = [ctypes.c_int32, ctypes.c_uint64, i32p]
+            lib.gg_king.argtypes = [ctypes.c_int32, i32p, i32p]
             vp = ctypes.c_void_p
             lib.gg_batch.argtypes = [ctypes.c_int32, vp, vp, vp, vp, ctypes.c_uint64,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_double, i32p, i32p]
@@ -124,15 +125,12 @@ def king(M: int):
     Vertex id = row * M + col.  Each undirected edge is emitted once, so the
     list has (M - 1)(4M - 2) entries (Table II's edge column).
     """
-    r, c = np.meshgrid(np.arange(M, dtype=np.int64), np.arange(M, dtype=np.int64), indexing="ij")
-    r = r.ravel()
-    c = c.ravel()
-    src, dst = [], []
-    for dr, dc in ((0, 1), (1, -1), (1, 0), (1, 1)):
-        ok = (r + dr < M) & (c + dc >= 0) & (c + dc < M)
-        src.append(r[ok] * M + c[ok])
-        dst.append((r[ok] + dr) * M + (c[ok] + dc))
-    return (np.concatenate(src).astype(np.int32), np.concatenate(dst).astype(np.int32), M * M)
+    m = (M - 1) * (4 * M - 2)
+    src = np.empty(m, dtype=np.int32)
+    dst = np.empty(m, dtype=np.int32)
+    if _load().gg_king(M, _p(src), _p(dst)) != 0:
+        raise ValueError(f"gg_king failed for M={M}")
+    return src, dst, M * M
 
 
 def complete(n: int):
@@ -274,6 +272,8 @@ class Workload:
             return er(self.n, self.m, self.seed)
         if self.family == "rmat":
             return rmat(self.scale, self.edgefactor, self.a, self.b, self.c, self.seed, True)
+        if self.family == "king":
+            return king(self.scale)
         raise ValueError(self.family)
 
 
@@ -289,6 +289,10 @@ WORKLOADS = {
         "rmat18", "rmat", n=1 << 18, scale=18, seed=1,
         description="R-MAT scale 18, edgefactor 16, permuted; count + support + full truss "
                     "decomposition (the small case for hardware-counter captures)"),
+    "king8192": Workload(
+        "king8192", "king", n=8192 * 8192, scale=8192, seed=0,
+        description="the 8192 x 8192 8-neighbour image graph (Section IV-C, Table II's family): "
+                    "268M edges, T = 4(M-1)^2; count + support + full truss decomposition"),
     "rmat24": Workload(
         "rmat24", "rmat", n=1 << 24, scale=24, seed=2, truss_ks=(3, 4, 6, 8),
         description="R-MAT scale 24, edgefactor 16 (268M draws), permuted; "

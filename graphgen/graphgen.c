@@ -213,3 +213,30 @@ int gg_batch(int32_t G, const int32_t* kind, const int32_t* n, const int64_t* m,
     }
     return bad ? -1 : 0;
 }
+
+/* The M x M 8-neighbour image graph (Section IV-C): vertex r*M + c; each
+ * undirected edge once, in four blocks by offset (0,+1), (+1,-1), (+1,0),
+ * (+1,+1), row-major within a block; (M - 1)(4M - 2) pairs in all. */
+int gg_king(int32_t M, int32_t* src, int32_t* dst) {
+    if (M < 1 || (int64_t)M * M > 2147483647LL) return -1;
+    const int64_t m1 = (int64_t)M - 1;
+    const int64_t cnt[4] = {(int64_t)M * m1, m1 * m1, m1 * (int64_t)M, m1 * m1};
+    const int dr[4] = {0, 1, 1, 1}, dc[4] = {1, -1, 0, 1};
+    int64_t base = 0;
+    for (int d = 0; d < 4; ++d) {
+        const int c0 = dc[d] < 0 ? 1 : 0;                /* first column of a row */
+        const int ncol = dc[d] == 0 ? M : M - 1;          /* columns per row */
+        const int nrow = dr[d] == 0 ? M : M - 1;
+#pragma omp parallel for schedule(static)
+        for (int32_t r = 0; r < nrow; ++r) {
+            int64_t i = base + (int64_t)r * ncol;
+            for (int32_t k = 0; k < ncol; ++k, ++i) {
+                const int32_t c = c0 + k;
+                src[i] = r * M + c;
+                dst[i] = (r + dr[d]) * M + (c + dc[d]);
+            }
+        }
+        base += cnt[d];
+    }
+    return 0;
+}

@@ -226,7 +226,8 @@ typedef struct {
     int64_t query_ns;          /* supports + per-graph sums + peel */
     int64_t m;                 /* edges of all graphs after cleaning */
     int64_t triangles;         /* triangles of all graphs */
-    int32_t intersect_form;    /* 1 = row/hash kernel, 2 = edge-per-warp kernel */
+    int32_t intersect_form;    /* 1 = row/hash kernel, 2 = edge-per-warp kernel,
+                                  3 = edge-per-thread kernel */
     int32_t peel_form;         /* 0 = no peel, 1 = triangle lists, 2 = intersections */
     int32_t tuned_from_cache;  /* 1 if the kernel choice came from the tuner's cache */
     int32_t captured;          /* 1 if the query ran as one CUDA graph launch */
@@ -307,11 +308,14 @@ int64_t tc_debug_fail_alloc(int64_t nth);
 int tc_debug_peel_mode(int mode);
 
 /*
- * Test hook: which kernel tc_count / tc_edge_support use.  0 = automatic
- * (one block per row with its out-list in a shared-memory hash table when
- * the largest out-list fits, else one warp per oriented edge), 1 = the
- * row kernel where the graph allows it, 2 = always one warp per edge.  Both
- * give the same results.  Returns the previous mode.
+ * Test hook: which kernel tc_count / tc_edge_support (and the triangle-list
+ * build of the peel) use.  0 = automatic (one thread per oriented edge
+ * merging the two out-lists when the largest out-list has at most 16
+ * entries; else one block per row with its out-list in a shared-memory hash
+ * table when the largest out-list fits; else one warp per oriented edge),
+ * 1 = the row kernel where the graph allows it, 2 = always one warp per
+ * edge, 3 = always one thread per edge.  All give the same results.
+ * Returns the previous mode.
  */
 int tc_debug_intersect_mode(int mode);
 

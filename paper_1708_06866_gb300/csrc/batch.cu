@@ -111,8 +111,9 @@ unsigned grid_items(int64_t n, int per = 256) {
 int autotune(Graph* g, int32_t k, Choice* c, cudaStream_t s) {
     // masked-product kernel
     int64_t best_ns = -1;
-    for (int form : {1, 2}) {
+    for (int form : {1, 2, 3}) {
         if (form == 1 && !triangle_lists_supported(g)) continue;  // the row kernel's limit
+        if (form == 3 && g->max_out > 64) continue;  // merges grow with the out-lists
         int64_t T = 0;
         TC_TRY(compute_support(g, g->support, true, &T, s, form));
         g->triangles = T;

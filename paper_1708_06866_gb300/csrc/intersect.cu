@@ -47,6 +47,7 @@ constexpr int RX_THREADS = TC_RX_THREADS;
 constexpr int RX_WARPS = RX_THREADS / 32;
 constexpr int RX_MAX_OUT = 8192;  // largest |N+(u)| the shared table holds (load <= 1/2)
 constexpr int IX_THREADS = 256;
+constexpr int THREAD_MAX_OUT = 16;  // largest out-list for which a thread per edge is used
 
 enum Mode { COUNT = 0, SUPPORT = 1, LISTS = 2 };
 
@@ -205,6 +206,61 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
     if (threadIdx.x == 0) {
         unsigned long long t = 0;
         for (int w = 0; w < RX_WARPS; ++w) t += s_acc[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+// Small out-lists (the largest at most THREAD_MAX_OUT entries): one thread
+// per oriented edge (u, v) merges N+(u) and N+(v).  Each common w closes the
+// triangle u < v < w.  SUPPORT credits its three edges by atomics; LISTS
+// writes the triangle's pair into the three lists, each filled from its top
+// by a per-edge cursor.
+template <int MODE>
+__global__ void __launch_bounds__(IX_THREADS) k_edges_thread(
+    const int2* __restrict__ ends, const int64_t* __restrict__ rowptr,
+    const int64_t* __restrict__ upper, const int32_t* __restrict__ col,
+    const int32_t* __restrict__ eid, int64_t m, int32_t* __restrict__ sup,
+    unsigned int* __restrict__ top, int2* __restrict__ pairs,
+    unsigned long long* __restrict__ partials) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long acc = 0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        const int2 uv = ends[j];
+        int64_t a = upper[uv.x], b = upper[uv.y];
+        const int64_t a1 = rowptr[uv.x + 1], b1 = rowptr[uv.y + 1];
+        uint32_t c = 0;
+        while (a < a1 && b < b1) {
+            const int32_t x = col[a], y = col[b];
+            if (x < y) {
+                ++a;
+            } else if (x > y) {
+                ++b;
+            } else {
+                ++c;
+                if (MODE == SUPPORT) {
+                    atomicAdd(&sup[eid[a]], 1);
+                    atomicAdd(&sup[eid[b]], 1);
+                }
+                if (MODE == LISTS) {
+                    const int32_t e_uw = eid[a], e_vw = eid[b], e_uv = (int32_t)j;
+                    pairs[atomicSub(&top[e_uv], 1u) - 1u] = make_int2(e_uw, e_vw);
+                    pairs[atomicSub(&top[e_uw], 1u) - 1u] = make_int2(e_uv, e_vw);
+                    pairs[atomicSub(&top[e_vw], 1u) - 1u] = make_int2(e_uv, e_uw);
+                }
+                ++a;
+                ++b;
+            }
+        }
+        if (MODE == SUPPORT && c) atomicAdd(&sup[j], (int)c);
+        acc += c;
+    }
+    __shared__ unsigned long long s_acc[IX_THREADS / 32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) s_acc[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < IX_THREADS / 32; ++w) t += s_acc[w];
         partials[blockIdx.x] = t;
     }
 }
@@ -485,6 +541,19 @@ int graph_wedge_work(Graph* g, int64_t* out, cudaStream_t s) {
     return TC_OK;
 }
 
+// The intersection kernel a call uses: 1 = one block per row (hash table),
+// 2 = one warp per oriented edge, 3 = one thread per oriented edge.  form 0
+// (automatic, unless the test hook forces one): threads for small out-lists,
+// rows while the largest out-list fits the table, else warps.
+int concrete_form(const Graph* g, int form) {
+    const int f = form != 0 ? form : intersect_mode();
+    if (f == 3) return 3;
+    if (f == 2) return 2;
+    if (f == 1) return g->max_out <= RX_MAX_OUT ? 1 : 2;
+    if (g->max_out <= THREAD_MAX_OUT) return 3;
+    return g->max_out <= RX_MAX_OUT ? 1 : 2;
+}
+
 int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangles,
                     cudaStream_t s, int form) {
     const int64_t m = g->m;
@@ -492,8 +561,8 @@ int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangle
         if (triangles) *triangles = 0;
         return TC_OK;
     }
-    const int f = form != 0 ? form : intersect_mode();
-    const bool rows = g->max_out <= RX_MAX_OUT && f != 2;
+    const int f = concrete_form(g, form);
+    const bool rows = f == 1;
     const int blocks = rows ? rows_blocks(g, want_support ? SUPPORT : COUNT) : num_sms() * 8;
     Scratch sc(s);
     unsigned long long* partials;
@@ -505,6 +574,15 @@ int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangle
         if (want_support)
             TC_TRY(launch_rows<SUPPORT>(g, sup, nullptr, nullptr, nullptr, partials, blocks, s));
         else TC_TRY(launch_rows<COUNT>(g, nullptr, nullptr, nullptr, nullptr, partials, blocks, s));
+    } else if (f == 3) {
+        if (want_support)
+            k_edges_thread<SUPPORT><<<blocks, IX_THREADS, 0, s>>>(
+                g->ends, g->rowptr, g->upper, g->col, g->eid, m, sup, nullptr, nullptr, partials);
+        else
+            k_edges_thread<COUNT><<<blocks, IX_THREADS, 0, s>>>(
+                g->ends, g->rowptr, g->upper, g->col, g->eid, m, nullptr, nullptr, nullptr,
+                partials);
+        TC_LAUNCH_CHECK("k_edges_thread");
     } else if (want_support) {
         k_edges_warp<true><<<blocks, IX_THREADS, 0, s>>>(g->ends, g->rowptr, g->upper,
                                                          g->col, g->eid, m, sup, partials);
@@ -552,7 +630,8 @@ int plan_triangle_lists(Graph* g, Scratch& sc, ListsPlan* lp) {
     lp->chunks = (m + SC_CHUNK - 1) / SC_CHUNK;
     TC_TRY(sc.alloc(&lp->sums, lp->chunks));
     TC_TRY(sc.alloc(&lp->top, m));
-    lp->blocks = rows_blocks(g, LISTS);
+    lp->thread = concrete_form(g, 0) == 3;
+    lp->blocks = lp->thread ? num_sms() * 8 : rows_blocks(g, LISTS);
     TC_TRY(sc.alloc(&lp->partials, lp->blocks));
     return TC_OK;
 }
@@ -574,7 +653,14 @@ int enqueue_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off
                      s>>>(off + 1, m, lp->top);
     TC_LAUNCH_CHECK("k_u32_from_u64");
     TC_TRY(lp->timer.start(s));
-    TC_TRY(launch_rows<LISTS>(g, nullptr, off, lp->top, pairs, lp->partials, lp->blocks, s));
+    if (lp->thread) {
+        k_edges_thread<LISTS><<<lp->blocks, IX_THREADS, 0, s>>>(
+            g->ends, g->rowptr, g->upper, g->col, g->eid, m, nullptr, lp->top, pairs,
+            lp->partials);
+        TC_LAUNCH_CHECK("k_edges_thread");
+    } else {
+        TC_TRY(launch_rows<LISTS>(g, nullptr, off, lp->top, pairs, lp->partials, lp->blocks, s));
+    }
     TC_TRY(lp->timer.stop(s));
     return TC_OK;
 }

@@ -38,6 +38,14 @@ constexpr int PK_THREADS = TC_PK_THREADS;
 constexpr int PK_WARPS = PK_THREADS / 32;
 constexpr int WINDOW = 8;        // support values one full scan covers (see k_peel)
 constexpr int64_t HEAVY = 4096;  // triangle-list length above which an edge is "heavy"
+#ifndef TC_PK_LANE_EDGES
+#define TC_PK_LANE_EDGES 8           // frontier edges per warp from which lanes take one each
+#endif
+#ifndef TC_PK_SHORT_LIST
+#define TC_PK_SHORT_LIST 32          // ... and walk lists up to this length alone
+#endif
+constexpr int64_t LANE_EDGES = TC_PK_LANE_EDGES;
+constexpr int64_t SHORT_LIST = TC_PK_SHORT_LIST;
 #ifndef TC_PK_UNROLL
 #define TC_PK_UNROLL 2               // triangle-list entries per lane in flight
 #endif
@@ -287,6 +295,9 @@ __device__ __forceinline__ void process_edge(const PeelArgs& a, Round rd, int32_
             if (one_warp) {
                 seen += __reduce_add_sync(0xffffffffu, (unsigned)found);
                 if (seen >= live) break;
+            } else if (gsize == 1) {  // one lane alone
+                seen += found;
+                if (seen >= live) break;
             }
         }
         return;
@@ -347,6 +358,26 @@ __device__ __forceinline__ void process_list(const PeelArgs& a, Round rd, const 
                                              int64_t nL, int64_t gwarp, int64_t nwarps,
                                              const Sinks& k, Tally& tl) {
     if (nL == 0) return;
+    if (TL && nL >= nwarps * LANE_EDGES) {
+        // many edges per warp: each lane takes one; lists of up to
+        // SHORT_LIST entries are walked by their lane alone, longer ones by
+        // the whole warp, one after another
+        const int lane = threadIdx.x & 31;
+        for (int64_t base = gwarp * 32; base < nL; base += nwarps * 32) {
+            const int64_t j = base + lane;
+            const int32_t e = j < nL ? ld_cg(L + j) : -1;
+            const bool longer =
+                e >= 0 && (int64_t)(a.off[e + 1] - a.off[e]) > SHORT_LIST;
+            if (e >= 0 && !longer) process_edge<TL>(a, rd, e, 0, 1, k, tl);
+            unsigned rest = __ballot_sync(0xffffffffu, longer);
+            while (rest) {
+                const int src = __ffs(rest) - 1;
+                rest &= rest - 1;
+                process_edge<TL>(a, rd, __shfl_sync(0xffffffffu, e, src), lane, 32, k, tl);
+            }
+        }
+        return;
+    }
     int64_t W = 1;
     while (nL * (W * 2) <= nwarps) W *= 2;
     const int64_t ngroups = nwarps / W;

@@ -272,6 +272,7 @@ struct ListsPlan {
     unsigned long long* sums = nullptr;  // per-chunk sums of the offset scan
     int64_t chunks = 0;
     unsigned int* top = nullptr;         // per-edge fill positions from the list's end
+    bool thread = false;                 // built by the thread-per-edge kernel
     unsigned long long* partials = nullptr;
     int blocks = 0;
     KernelTimer timer;

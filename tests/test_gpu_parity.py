@@ -45,12 +45,17 @@ def gpu_all(src, dst, n, ks=(2, 3, 4, 5, 6)):
         T_warp = tc.tc_count(g)
         s_warp, _ = tc.tc_edge_support(g)
         s_warp = s_warp.cpu().numpy()
+        tc.tc_debug_intersect_mode(3)   # the thread-per-edge kernel
+        T_thread = tc.tc_count(g)
+        s_thread, _ = tc.tc_edge_support(g)
+        s_thread = s_thread.cpu().numpy()
     finally:
         tc.tc_debug_intersect_mode(prev)
     T = tc.tc_count(g)
     s, T2 = tc.tc_edge_support(g)
     out = dict(m=g.m, lo=lo.cpu().numpy(), hi=hi.cpu().numpy(), T=T, T2=T2,
-               s=s.cpu().numpy(), peel={}, T_warp=T_warp, s_warp=s_warp)
+               s=s.cpu().numpy(), peel={}, T_warp=T_warp, s_warp=s_warp, T_thread=T_thread,
+               s_thread=s_thread)
     for name, mode in PEEL_MODES.items():
         prev = tc.tc_debug_peel_mode(mode)
         try:
@@ -81,6 +86,7 @@ def check(src, dst, n, ks=(2, 3, 4, 5, 6)):
     assert got["T"] == T and got["T2"] == T and got["T_warp"] == T
     assert np.array_equal(got["s"], og.support())
     assert np.array_equal(got["s_warp"], got["s"])
+    assert got["T_thread"] == T and np.array_equal(got["s_thread"], got["s"])
     kmax, truss = og.truss_decomposition()
     for name, res in got["peel"].items():
         for k in ks:
@@ -402,3 +408,23 @@ def test_resume_across_forms():
     check_k(4, L)                             # smaller k: fresh
     check_k(6, L)                             # resumes from k = 4
     tc.tc_graph_free(g)
+
+
+def test_every_intersection_kernel_builds_the_same_lists():
+    """The triangle lists of the peel, built by each intersection kernel
+    (forced by the test hook, also on a skewed graph where the automatic
+    choice would not take it), give the oracle's truss decomposition."""
+    src, dst, n = graphgen.rmat(12, 16, seed=5)
+    og = oracle.OracleGraph.from_edges(src, dst, n)
+    want_kmax, want_truss = og.truss_decomposition()
+    for imode in (1, 2, 3):
+        g = tc.tc_build_csr(dev(src), dev(dst), n)
+        pi = tc.tc_debug_intersect_mode(imode)
+        pp = tc.tc_debug_peel_mode(PEEL_MODES["lists"])
+        try:
+            kmax, truss = tc.ktruss_max(g)
+        finally:
+            tc.tc_debug_intersect_mode(pi)
+            tc.tc_debug_peel_mode(pp)
+        assert kmax == want_kmax and np.array_equal(truss.cpu().numpy(), want_truss), imode
+        tc.tc_graph_free(g)
