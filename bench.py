@@ -56,7 +56,8 @@ class ClockSampler:
     """Samples nvidia-smi clocks and throttle reasons while running."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+              "memory.used")
 
     def __init__(self, index: int):
         self.index = index
@@ -106,6 +107,33 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+    def _column(self, i):
+        out = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            try:
+                out.append(float(parts[i]))
+            except (IndexError, ValueError):
+                pass
+        return out
+
+    def energy(self, ms_per_step: float, units_per_step: float) -> dict:
+        """Board power sampled during the timed loop, as energy per step
+        (mean power x device time of a step) and units per joule."""
+        pw = self._column(2)
+        if not pw:
+            return {"mean_power_w": None, "samples": 0}
+        p = float(np.mean(pw))
+        j = p * ms_per_step / 1e3
+        return {"mean_power_w": round(p, 1), "joules_per_step": round(j, 4),
+                "edges_per_joule": units_per_step / j if j > 0 else None, "samples": len(pw),
+                "source": "nvidia-smi power.draw every 200 ms during the timed loop "
+                          "(whole board, idle share included)"}
+
+    def memory_used_mib(self):
+        mu = self._column(8)
+        return max(mu) if mu else None
 
 
 # ------------------------------------------------------------------ ranks
@@ -438,7 +466,14 @@ def bench_ours(args, rank, world):
            "phases_ms": {k: round(float(np.mean(v)), 3) for k, v in phases.items()},
            "roofline": roofline, "kernels": kernels, "peel_work_per_launch": peel_work,
            "gpu_launches": launches,
-           "clocks": sampler.summary()}
+           "clocks": sampler.summary(),
+           # the paper's other measures (Section IV): energy, memory, processor
+           "energy": sampler.energy(ms_per_step, m),
+           "memory": {"graph_device_bytes": max(int(i.get("device_bytes") or 0) for i in infos)
+                      if infos else None,
+                      "device_used_mib_max": sampler.memory_used_mib()},
+           "processor": {"name": torch.cuda.get_device_name(local),
+                         "sms": torch.cuda.get_device_properties(local).multi_processor_count}}
 
     if not args.no_e2e:
         out["e2e"] = bench_e2e(args, tc, torch, src_h, dst_h, n, wl, stream)
