@@ -203,6 +203,30 @@ int tc_graph_wedge_work(tc_graph* g, int64_t* out, void* cuda_stream);
  */
 int tc_graph_set_memory_limit(tc_graph* g, int64_t bytes);
 
+/*
+ * Reads an edge list from a file (Section II's inputs): format 1 = the
+ * Graph Challenge's tab-separated lines "u v [weight]", 2 = a Matrix Market
+ * coordinate file ("%%MatrixMarket matrix coordinate ..." header, a
+ * "rows cols entries" size line, then "i j [value]" lines), 0 = by the
+ * file name (.mtx / .mm: Matrix Market, else tab-separated).  Ids in the
+ * file are 1-based and are written 0-based; weights and values are ignored
+ * (any listed pair is an edge); blank lines and comment lines ('%', and '#'
+ * in tab-separated files) are skipped.  Entries are written in file order,
+ * with nothing cleaned: pass the arrays to tc_build_csr.
+ *   src, dst:  host int32 arrays of `capacity` entries, or both NULL to only
+ *              count (call once with NULL to size the arrays);
+ *   m_out:     entries in the file;
+ *   n_out:     vertex count: the largest id in a tab-separated file, the
+ *              declared size in a Matrix Market file.
+ * Host code only (no device work).  Errors: TC_EINVAL (NULL path or
+ * outputs, unreadable file, a malformed line — the message names it —, a
+ * Matrix Market entry count other than the declared one, capacity smaller
+ * than the entries), TC_ERANGE (an id of 0, above 2^31 - 1, or outside the
+ * declared matrix size).
+ */
+int tc_read_edges(const char* path, int format, int32_t* src, int32_t* dst, int64_t capacity,
+                  int64_t* m_out, int32_t* n_out);
+
 /* Number of CUDA kernels the library has launched in this process (all
  * graphs, all threads); lets a caller count the launches of a region. */
 int64_t tc_launch_count(void);

@@ -30,7 +30,7 @@ __all__ = [
     "TCError", "Graph", "load_library", "library_path", "tc_build_csr", "tc_count",
     "tc_edge_support", "ktruss", "ktruss_max", "tc_num_edges", "tc_num_vertices", "tc_edges",
     "tc_graph_info", "tc_graph_wedge_work", "tc_launch_count", "tc_batch_run",
-    "tc_graph_set_memory_limit",
+    "tc_graph_set_memory_limit", "tc_read_edges",
     "tc_graph_free", "tc_strerror", "tc_last_error", "tc_debug_fail_alloc",
     "tc_debug_spin_limit_ns", "tc_debug_peel_mode", "tc_debug_intersect_mode", "TC_OK", "TC_EINVAL", "TC_ERANGE", "TC_ENOMEM", "TC_ECUDA",
     "TC_ETIMEDOUT", "TC_EOVERFLOW", "TC_INPUT_AUTO", "TC_INPUT_DEVICE", "TC_INPUT_HOST",
@@ -75,6 +75,8 @@ def load_library(build_if_missing: bool = True):
             "tc_graph_info": (ctypes.c_int, [vp, ctypes.POINTER(GraphInfo), vp]),
             "tc_launch_count": (i64, []),
             "tc_graph_set_memory_limit": (ctypes.c_int, [vp, i64]),
+            "tc_read_edges": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, vp, vp, i64,
+                                             ctypes.POINTER(i64), ctypes.POINTER(i32)]),
             "tc_batch_run": (ctypes.c_int, [ctypes.POINTER(BatchDesc), vp]),
             "tc_graph_wedge_work": (ctypes.c_int, [vp, ctypes.POINTER(i64), vp]),
             "tc_debug_fail_alloc": (i64, [i64]),
@@ -320,6 +322,22 @@ def tc_graph_set_memory_limit(g: Graph, nbytes: int):
     """Bound on the optional device memory (triangle lists, caches) for this graph; <0 = auto."""
     _check(load_library().tc_graph_set_memory_limit(g.handle, int(nbytes)),
            "tc_graph_set_memory_limit")
+
+
+def tc_read_edges(path: str, fmt: int = 0):
+    """Edge list of a tab-separated or Matrix Market file (1-based ids in the
+    file) as 0-based int32 numpy arrays: returns (src, dst, n)."""
+    lib = load_library()
+    m = ctypes.c_int64()
+    n = ctypes.c_int32()
+    bpath = os.fsencode(path)
+    _check(lib.tc_read_edges(bpath, int(fmt), None, None, 0, ctypes.byref(m), ctypes.byref(n)),
+           "tc_read_edges")
+    src = np.empty(m.value, dtype=np.int32)
+    dst = np.empty(m.value, dtype=np.int32)
+    _check(lib.tc_read_edges(bpath, int(fmt), src.ctypes.data, dst.ctypes.data, m.value,
+                             ctypes.byref(m), ctypes.byref(n)), "tc_read_edges")
+    return src, dst, n.value
 
 
 def tc_launch_count() -> int:

@@ -428,3 +428,23 @@ def test_every_intersection_kernel_builds_the_same_lists():
             tc.tc_debug_peel_mode(pp)
         assert kmax == want_kmax and np.array_equal(truss.cpu().numpy(), want_truss), imode
         tc.tc_graph_free(g)
+
+
+def test_from_a_tab_separated_file(tmp_path):
+    """The Graph Challenge's input path: a 1-based tab-separated file with
+    both directions of every edge and unit weights (Section II), read by
+    tc_read_edges and built on the device: the 16 x 16 image graph gives
+    Table II's edge count and the closed-form triangles."""
+    M = 16
+    s, d, n = graphgen.king(M)
+    rows = np.concatenate([np.stack([s, d], 1), np.stack([d, s], 1)]) + 1
+    path = tmp_path / "king16.tsv"
+    path.write_text("".join(f"{u}\t{v}\t1\n" for u, v in rows.tolist()))
+    src, dst, n2 = tc.tc_read_edges(str(path))
+    assert n2 == n and len(src) == 2 * len(s)
+    g = tc.tc_build_csr(dev(src), dev(dst), n2)
+    assert g.m == (M - 1) * (4 * M - 2)
+    assert tc.tc_count(g) == 4 * (M - 1) ** 2
+    kmax, _ = tc.ktruss_max(g)
+    assert kmax == 4
+    tc.tc_graph_free(g)
