@@ -69,6 +69,8 @@ def _bind(lib):
     lib.oracle_ktruss.restype = ctypes.c_int64
     lib.oracle_truss_decomposition.argtypes = [vp, i32p]
     lib.oracle_truss_decomposition.restype = ctypes.c_int32
+    lib.oracle_truss_components.argtypes = [vp, u8p, i32p, i32p]
+    lib.oracle_truss_components.restype = ctypes.c_int64
     return lib
 
 
@@ -182,6 +184,22 @@ class OracleGraph:
         if left < 0:
             raise ValueError("k < 2")
         return mask, sup, int(left)
+
+    def components(self, mask):
+        """Connected components of the subgraph of the edges with mask 1:
+        (edge labels int32[m], vertex labels int32[n], count); a label is the
+        smallest vertex id of the component, -1 outside the subgraph."""
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        el = np.empty(self.m, dtype=np.int32)
+        vl = np.empty(self.n, dtype=np.int32)
+        c = self._lib.oracle_truss_components(self._h, _ptr(mk, ctypes.c_uint8),
+                                              _ptr(el, ctypes.c_int32), _ptr(vl, ctypes.c_int32))
+        return el, vl, int(c)
+
+    def ktruss_components(self, k: int):
+        """Connected components of the k-truss (see components)."""
+        mask, _, _ = self.ktruss(k)
+        return self.components(mask)
 
     def truss_decomposition(self):
         """(kmax, truss int32[m]): truss[e] = largest k whose k-truss holds e."""

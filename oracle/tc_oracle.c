@@ -366,3 +366,52 @@ int32_t oracle_truss_decomposition(const oracle_graph* g, int32_t* truss) {
     free(pb);
     return kmax;
 }
+
+/* Connected components of the subgraph formed by the edges with alive[e] = 1
+ * (the k-truss as a set of connected trusses, Section IV-A's enumeration of
+ * k-trusses).  A component is the set of vertices reachable from one another
+ * through alive edges, with the alive edges among them.  Vertices are
+ * visited in increasing id and a search starts at each vertex with an alive
+ * edge not yet reached, so the vertex that starts a component is its
+ * smallest id; that id labels the component.
+ *   edge_label[e]   = label of e's component, or -1 if e is not alive;
+ *   vertex_label[v] = label of v's component, or -1 if v has no alive edge
+ *                     (may be NULL).
+ * Returns the number of components. */
+int64_t oracle_truss_components(const oracle_graph* g, const uint8_t* alive,
+                                int32_t* edge_label, int32_t* vertex_label) {
+    int32_t* lab = (int32_t*)malloc(sizeof(int32_t) * (size_t)(g->n > 0 ? g->n : 1));
+    int32_t* stack = (int32_t*)malloc(sizeof(int32_t) * (size_t)(g->n > 0 ? g->n : 1));
+    int64_t comps = 0;
+    for (int32_t v = 0; v < g->n; ++v) lab[v] = -1;
+    for (int32_t v = 0; v < g->n; ++v) {
+        if (lab[v] >= 0) continue;
+        int has = 0;
+        for (int64_t p = g->off[v]; p < g->off[v + 1]; ++p)
+            if (alive[g->eid[p]]) {
+                has = 1;
+                break;
+            }
+        if (!has) continue;
+        ++comps;
+        int64_t top = 0;
+        lab[v] = v;
+        stack[top++] = v;
+        while (top > 0) {
+            const int32_t x = stack[--top];
+            for (int64_t p = g->off[x]; p < g->off[x + 1]; ++p) {
+                const int32_t y = g->nbr[p];
+                if (alive[g->eid[p]] && lab[y] < 0) {
+                    lab[y] = v;
+                    stack[top++] = y;
+                }
+            }
+        }
+    }
+    for (int64_t e = 0; e < g->m; ++e) edge_label[e] = alive[e] ? lab[g->lo[e]] : -1;
+    if (vertex_label)
+        for (int32_t v = 0; v < g->n; ++v) vertex_label[v] = lab[v];
+    free(lab);
+    free(stack);
+    return comps;
+}

@@ -16,8 +16,9 @@ import pytest
 import graphgen
 import oracle
 from conftest import ROOT
-from test_oracle_pins import (brute_support, brute_triangles, dense_adj, king_support,
-                              literal_algorithm4, small_random_graphs)
+from test_oracle_pins import (brute_support, brute_triangles, closure_components, dense_adj,
+                              king_support, literal_algorithm4, small_random_graphs,
+                              two_cliques_and_a_bridge)
 
 SRC = os.path.join(ROOT, "oracle", "tc_oracle.c")
 
@@ -36,6 +37,10 @@ MUTANTS = [
      "            --s[h];\n", ""),
     ("truss number off by one",
      "if (level) level[e] = k - 1;", "if (level) level[e] = k;"),
+    ("components ignore the edge subset",
+     "if (alive[g->eid[p]] && lab[y] < 0) {", "if (lab[y] < 0) {"),
+    ("component start vertex labelled apart from the rest",
+     "lab[v] = v;\n        stack[top++] = v;", "lab[v] = v + 1;\n        stack[top++] = v;"),
     ("adjacency drops the reverse direction",
      "tmp[g->off[b] + fill[b]++] = (nbr_entry){a, (int32_t)e};",
      "tmp[g->off[b] + fill[b]++] = (nbr_entry){b, (int32_t)e};"),
@@ -58,6 +63,18 @@ def pins_fail(lib) -> bool:
                     mask, sup, _ = g.ktruss(k)
                     if not (np.array_equal(mask, mref) and np.array_equal(sup, sref)):
                         return True
+        for n, lo, hi in small_random_graphs(10, 20, seed=12):
+            g = oracle.OracleGraph(n, lo, hi, lib=lib)
+            mk = g.ktruss(3)[0]
+            got = g.components(mk)
+            want = closure_components(n, lo, hi, mk)
+            if got[2] != want[2] or not (np.array_equal(got[0], want[0])
+                                         and np.array_equal(got[1], want[1])):
+                return True
+        s, d, n = two_cliques_and_a_bridge()
+        g = oracle.OracleGraph.from_edges(s, d, n, lib=lib)
+        if g.ktruss_components(5)[2] != 2:
+            return True
         for M in (4, 9):
             s, d, n = graphgen.king(M)
             g = oracle.OracleGraph.from_edges(s, d, n, lib=lib)

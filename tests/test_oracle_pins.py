@@ -392,3 +392,66 @@ def test_edges_outside_a_truss_close_too_few_triangles_with_it():
         out = np.flatnonzero(mask == 0)
         if len(out):
             assert (g.support_within_of(mask, out) < k - 2).all()
+
+
+# ------------------------------------------------------- truss components
+
+def closure_components(n, lo, hi, mask):
+    """Connected components of the masked edges by boolean reachability
+    (squaring I + A until it is stable), independent of the oracle's search:
+    label = smallest vertex reachable, -1 for vertices without a masked edge."""
+    sel = np.asarray(mask).astype(bool)
+    R = np.eye(n, dtype=bool)
+    R[lo[sel], hi[sel]] = True
+    R[hi[sel], lo[sel]] = True
+    while True:
+        R2 = (R.astype(np.int64) @ R.astype(np.int64)) > 0
+        if (R2 == R).all():
+            break
+        R = R2
+    touched = np.zeros(n, dtype=bool)
+    touched[lo[sel]] = True
+    touched[hi[sel]] = True
+    vl = np.where(touched, R.argmax(axis=1), -1).astype(np.int32)
+    el = np.where(sel, vl[lo] if len(lo) else np.zeros(0, np.int32), -1).astype(np.int32)
+    return el, vl, len(set(vl[touched].tolist()))
+
+
+def test_components_match_reachability():
+    rng = np.random.default_rng(8)
+    for n, lo, hi in small_random_graphs(40, 30, seed=7):
+        g = oracle.OracleGraph(n, lo, hi)
+        masks = [rng.random(len(lo)) < 0.3, np.ones(len(lo), bool)]
+        masks += [g.ktruss(k)[0] for k in (3, 4)]
+        for mk in masks:
+            el, vl, c = g.components(mk)
+            wel, wvl, wc = closure_components(n, lo, hi, mk)
+            assert c == wc and np.array_equal(el, wel) and np.array_equal(vl, wvl)
+
+
+def two_cliques_and_a_bridge():
+    """K5 on 0..4, K5 on 10..14, a path 4-5-6-...-10 between them (n = 15)."""
+    pairs = [(a, b) for a in range(5) for b in range(a + 1, 5)]
+    pairs += [(a, b) for a in range(10, 15) for b in range(a + 1, 15)]
+    pairs += [(i, i + 1) for i in range(4, 10)]
+    s, d = np.array(pairs, dtype=np.int32).T
+    return s, d, 15
+
+
+def test_components_closed_forms():
+    s, d, n = two_cliques_and_a_bridge()
+    g = oracle.OracleGraph.from_edges(s, d, n)
+    el, vl, c = g.ktruss_components(5)     # each K5: every edge in 3 triangles
+    assert c == 2
+    assert sorted(set(el[el >= 0].tolist())) == [0, 10] and (el >= 0).sum() == 20
+    assert vl.tolist() == [0] * 5 + [-1] * 5 + [10] * 5
+    el, vl, c = g.ktruss_components(2)     # the 2-truss: one component
+    assert c == 1 and (el == 0).all()
+    assert g.ktruss_components(6)[2] == 0
+    for M in (3, 6):
+        s, d, n = graphgen.king(M)
+        g = oracle.OracleGraph.from_edges(s, d, n)
+        el, vl, c = g.ktruss_components(4)
+        assert c == 1 and (el == 0).all() and (vl == 0).all()
+        el, vl, c = g.ktruss_components(5)
+        assert c == 0 and (el == -1).all() and (vl == -1).all()
