@@ -204,6 +204,25 @@ int tc_graph_wedge_work(tc_graph* g, int64_t* out, void* cuda_stream);
 int tc_graph_set_memory_limit(tc_graph* g, int64_t bytes);
 
 /*
+ * The k-truss as connected trusses (Section IV-A: "enumerating all
+ * k-trusses"; the k-truss of ktruss() may fall apart into several connected
+ * pieces).  Computes the k-truss (as ktruss(), sharing its cache), then the
+ * connected components of the subgraph of its edges.  A component is
+ * labelled by its smallest vertex id (original ids).
+ *   edge_label_out:   m entries in canonical edge order (device or host):
+ *                     the label of the edge's component, -1 for an edge
+ *                     outside the k-truss; may be NULL only when m = 0;
+ *   vertex_label_out: n entries (device or host, may be NULL): the label of
+ *                     the vertex's component, -1 for a vertex with no
+ *                     k-truss edge;
+ *   count_out:        number of components (host).
+ * Synchronises the stream.  Errors: TC_EINVAL (NULL graph, count_out or
+ * edge_label_out, k < 2), TC_ENOMEM, TC_ECUDA, TC_ETIMEDOUT.
+ */
+int ktruss_components(tc_graph* g, int32_t k, int32_t* edge_label_out, int32_t* vertex_label_out,
+                      int64_t* count_out, void* cuda_stream);
+
+/*
  * Reads an edge list from a file (Section II's inputs): format 1 = the
  * Graph Challenge's tab-separated lines "u v [weight]", 2 = a Matrix Market
  * coordinate file ("%%MatrixMarket matrix coordinate ..." header, a

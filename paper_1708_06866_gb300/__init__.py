@@ -28,7 +28,7 @@ from . import _build
 
 __all__ = [
     "TCError", "Graph", "load_library", "library_path", "tc_build_csr", "tc_count",
-    "tc_edge_support", "ktruss", "ktruss_max", "tc_num_edges", "tc_num_vertices", "tc_edges",
+    "tc_edge_support", "ktruss", "ktruss_max", "ktruss_components", "tc_num_edges", "tc_num_vertices", "tc_edges",
     "tc_graph_info", "tc_graph_wedge_work", "tc_launch_count", "tc_batch_run",
     "tc_graph_set_memory_limit", "tc_read_edges",
     "tc_graph_free", "tc_strerror", "tc_last_error", "tc_debug_fail_alloc",
@@ -75,6 +75,7 @@ def load_library(build_if_missing: bool = True):
             "tc_graph_info": (ctypes.c_int, [vp, ctypes.POINTER(GraphInfo), vp]),
             "tc_launch_count": (i64, []),
             "tc_graph_set_memory_limit": (ctypes.c_int, [vp, i64]),
+            "ktruss_components": (ctypes.c_int, [vp, i32, vp, vp, ctypes.POINTER(i64), vp]),
             "tc_read_edges": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, vp, vp, i64,
                                              ctypes.POINTER(i64), ctypes.POINTER(i32)]),
             "tc_batch_run": (ctypes.c_int, [ctypes.POINTER(BatchDesc), vp]),
@@ -269,6 +270,22 @@ def ktruss(g: Graph, k: int, out=None, stream=None):
                                _stream_handle(stream))
     _check(rc, "ktruss")
     return out, left.value
+
+
+def ktruss_components(g: Graph, k: int, stream=None, vertices: bool = True):
+    """Connected components of the k-truss: (edge labels int32[m] in
+    canonical order, vertex labels int32[n] or None, count); a label is the
+    component's smallest vertex id, -1 outside the k-truss."""
+    torch = _torch()
+    dev = g.device
+    el = torch.empty(max(g.m, 0), dtype=torch.int32, device=dev)
+    vl = torch.empty(g.n, dtype=torch.int32, device=dev) if vertices else None
+    c = ctypes.c_int64()
+    _check(load_library().ktruss_components(g.handle, int(k), _ptr(el) if g.m else None,
+                                            _ptr(vl) if vl is not None else None,
+                                            ctypes.byref(c), _stream_handle(stream)),
+           "ktruss_components")
+    return el, vl, c.value
 
 
 def ktruss_max(g: Graph, out=None, stream=None, want_truss: bool = True):

@@ -277,6 +277,28 @@ int ktruss(tc_graph* g, int32_t k, uint8_t* mask_out, int64_t* edges_out, void* 
     return tc::check_dev_err(gg->dev_err, s);
 }
 
+int ktruss_components(tc_graph* g, int32_t k, int32_t* edge_label_out, int32_t* vertex_label_out,
+                      int64_t* count_out, void* cuda_stream) {
+    TC_TRY(begin_call(g, cuda_stream));
+    if (k < 2) return fail(TC_EINVAL, "k must be >= 2");
+    if (!count_out) return fail(TC_EINVAL, "count_out is NULL");
+    tc::Graph* gg = &g->g;
+    if (!edge_label_out && gg->m > 0) return fail(TC_EINVAL, "edge_label_out is NULL");
+    DeviceGuard dg(gg->device);
+    cudaStream_t s = as_stream(cuda_stream);
+    tc::Scratch sc(s);
+    int32_t* el = edge_label_out;
+    int32_t* vl = vertex_label_out;
+    const bool host_e = gg->m > 0 && tc::is_host_pointer(edge_label_out);
+    const bool host_v = vertex_label_out && tc::is_host_pointer(vertex_label_out);
+    if (host_e) TC_TRY(sc.alloc(&el, gg->m));
+    if (host_v) TC_TRY(sc.alloc(&vl, gg->n));
+    TC_TRY(tc::truss_components(gg, k, el, vl, count_out, s));
+    if (host_e) TC_TRY(deliver(edge_label_out, el, gg->m, s));
+    if (host_v) TC_TRY(deliver(vertex_label_out, vl, (int64_t)gg->n, s));
+    return tc::check_dev_err(gg->dev_err, s);
+}
+
 int ktruss_max(tc_graph* g, int32_t* kmax_out, int32_t* truss_out, void* cuda_stream) {
     TC_TRY(begin_call(g, cuda_stream));
     if (!kmax_out) return fail(TC_EINVAL, "kmax_out is NULL");

@@ -314,5 +314,9 @@ bool triangle_lists_supported(const Graph* g);
 int build_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off, int2* pairs,
                          cudaStream_t s);
 int peel_decompose(Graph* g, int32_t* truss_dev, int32_t* kmax, cudaStream_t s);
+// Connected components of the k-truss: canonical-order edge labels (device,
+// m), optional vertex labels (device, n); labels are smallest vertex ids.
+int truss_components(Graph* g, int32_t k, int32_t* edge_label, int32_t* vertex_label,
+                     int64_t* count, cudaStream_t s);
 
 }  // namespace tc

@@ -448,3 +448,63 @@ def test_from_a_tab_separated_file(tmp_path):
     kmax, _ = tc.ktruss_max(g)
     assert kmax == 4
     tc.tc_graph_free(g)
+
+
+def disjoint_union(parts):
+    """Vertex-disjoint union of (src, dst, n) graphs, vertex ids shifted."""
+    s_all, d_all, base = [], [], 0
+    for s, d, n in parts:
+        s_all.append(np.asarray(s, dtype=np.int64) + base)
+        d_all.append(np.asarray(d, dtype=np.int64) + base)
+        base += n
+    return (np.concatenate(s_all).astype(np.int32), np.concatenate(d_all).astype(np.int32), base)
+
+
+@pytest.mark.parametrize("case", ["cliques", "union", "rmat", "king", "er"])
+def test_ktruss_components_against_oracle(case):
+    """Connected trusses: every edge's and vertex's component label (its
+    smallest vertex id) and the component count equal the oracle's, for k
+    from 2 past kmax, with device and host outputs."""
+    from test_oracle_pins import two_cliques_and_a_bridge
+    if case == "cliques":
+        src, dst, n = two_cliques_and_a_bridge()
+    elif case == "union":
+        src, dst, n = disjoint_union([graphgen.complete(6), graphgen.king(5),
+                                      graphgen.rmat(8, seed=3), graphgen.complete(4),
+                                      graphgen.star(9)])
+    elif case == "rmat":
+        src, dst, n = graphgen.rmat(12, seed=9)
+    elif case == "king":
+        src, dst, n = graphgen.king(33)
+    else:
+        src, dst, n = graphgen.er(3000, 30000, seed=4)
+    og = oracle.OracleGraph.from_edges(src, dst, n)
+    kmax, _ = og.truss_decomposition()
+    g = tc.tc_build_csr(dev(src), dev(dst), n)
+    for k in range(2, kmax + 2):
+        wel, wvl, wc = og.ktruss_components(k)
+        el, vl, c = tc.ktruss_components(g, k)
+        assert c == wc, k
+        assert np.array_equal(el.cpu().numpy(), wel), k
+        assert np.array_equal(vl.cpu().numpy(), wvl), k
+    # host outputs through the ABI
+    k = max(3, kmax)
+    wel, wvl, wc = og.ktruss_components(k)
+    hel = np.empty(g.m, dtype=np.int32)
+    hvl = np.empty(n, dtype=np.int32)
+    import ctypes
+    cnt = ctypes.c_int64()
+    rc = tc.load_library().ktruss_components(g.handle, k, hel.ctypes.data, hvl.ctypes.data,
+                                             ctypes.byref(cnt), None)
+    assert rc == tc.TC_OK and cnt.value == wc
+    assert np.array_equal(hel, wel) and np.array_equal(hvl, wvl)
+    with pytest.raises(tc.TCError):
+        tc.ktruss_components(g, 1)
+    tc.tc_graph_free(g)
+
+
+def test_ktruss_components_without_edges():
+    g = tc.tc_build_csr(dev(np.array([2], np.int32)), dev(np.array([2], np.int32)), 5)
+    el, vl, c = tc.ktruss_components(g, 3)
+    assert c == 0 and len(el) == 0 and (vl.cpu().numpy() == -1).all()
+    tc.tc_graph_free(g)
