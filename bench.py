@@ -171,11 +171,13 @@ def run_step(tc, torch, src, dst, n, wl, stream, ev=None, outs=None, infos=None)
     mark("start")
     g = tc.tc_build_csr(src, dst, n, stream=stream)
     mark("build")
-    T = tc.tc_count(g, stream=stream)
-    mark("count")
+    # one masked-product pass gives the supports and T (Algorithm 4's s;
+    # T = sum(s) / 3); tc_count then returns the graph's known T
     sup_out = outs.get("support") if outs else None
     sup, T2 = tc.tc_edge_support(g, out=sup_out, stream=stream)
     mark("support")
+    T = tc.tc_count(g, stream=stream)
+    mark("count")
     res = {}
     if wl.truss_ks:
         for k in wl.truss_ks:
@@ -206,9 +208,9 @@ def kernel_rooflines(infos, count_bytes, support_bytes, lists_bytes, peak):
     acc = {}
     for inf in infos:
         for name, tkey, nbytes in (
-                ("masked product, count (k_rows<COUNT>)", "count_kernel_ns", count_bytes),
-                ("masked product, support (k_rows<SUPPORT>)", "support_kernel_ns", support_bytes),
-                ("triangle lists (k_rows<LISTS>)", "lists_kernel_ns", lists_bytes),
+                ("masked product, count", "count_kernel_ns", count_bytes),
+                ("masked product, support", "support_kernel_ns", support_bytes),
+                ("triangle lists", "lists_kernel_ns", lists_bytes),
                 ("peel (k_peel)", "peel_kernel_ns", inf.get("peel_bytes"))):
             t = inf.get(tkey)
             if t is None or t <= 0:

@@ -86,7 +86,9 @@ int tc_build_csr(const int32_t* src, const int32_t* dst, int64_t m_in, int32_t n
  *
  * Computes the masked product (L L^T) ∘ L over the degree-oriented adjacency
  * L (the once-per-triangle form of Algorithm 3): for every oriented edge
- * (u, v), |N+(u) ∩ N+(v)|, summed.  Exact int64.
+ * (u, v), |N+(u) ∩ N+(v)|, summed.  Exact int64.  A graph is immutable, so
+ * once T is known (an earlier tc_count, or tc_edge_support with
+ * triangles_out) it is returned without a launch.
  * triangles_out: host int64.  Synchronises the stream.
  */
 int tc_count(tc_graph* g, int64_t* triangles_out, void* cuda_stream);
@@ -94,7 +96,9 @@ int tc_count(tc_graph* g, int64_t* triangles_out, void* cuda_stream);
 /*
  * tc_edge_support — triangle support of every edge (Algorithm 4,
  * s = (R == 2) 1 with R = E A): s[e] = number of triangles containing e.
- * Every triangle found by the masked product credits its three edges.
+ * Every triangle found by the masked product credits its three edges; the
+ * same pass gives T.  The supports are computed once per graph and kept
+ * (later calls, and the peel, reuse them).
  * support_out: m int32 in edge-id order (device or host).
  * triangles_out: host int64, may be NULL (then, with a device support_out,
  * the call does not synchronise).

@@ -603,7 +603,8 @@ __global__ void k_truss_from_state(const int32_t* __restrict__ t,
 }
 
 int ensure_support_impl(Graph* g, cudaStream_t s) {
-    if (g->support_valid) return TC_OK;
+    // the peel needs the supports and T (it sizes the triangle lists by T)
+    if (g->support_valid && g->triangles >= 0) return TC_OK;
     if (!g->support) TC_TRY(dev_alloc_n(&g->support, g->m, s));
     int64_t T = 0;
     TC_TRY(compute_support(g, g->support, true, &T, s));

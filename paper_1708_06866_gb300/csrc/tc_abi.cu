@@ -225,6 +225,12 @@ int tc_count(tc_graph* g, int64_t* triangles_out, void* cuda_stream) {
     TC_TRY(begin_call(g, cuda_stream));
     if (!triangles_out) return fail(TC_EINVAL, "triangles_out is NULL");
     DeviceGuard dg(g->g.device);
+    // the graph is immutable: once its supports are computed, T is known
+    // (a kernel forced by the test hook is always run)
+    if (g->g.support_valid && g->g.triangles >= 0 && tc::intersect_mode() == 0) {
+        *triangles_out = g->g.triangles;
+        return TC_OK;
+    }
     int64_t T = 0;
     TC_TRY(tc::compute_support(&g->g, nullptr, false, &T, as_stream(cuda_stream)));
     g->g.triangles = T;
@@ -239,15 +245,19 @@ int tc_edge_support(tc_graph* g, int32_t* support_out, int64_t* triangles_out,
     if (!support_out && gg->m > 0) return fail(TC_EINVAL, "support_out is NULL");
     DeviceGuard dg(gg->device);
     cudaStream_t s = as_stream(cuda_stream);
-    if (!gg->support) TC_TRY(tc::dev_alloc_n(&gg->support, gg->m, s));
-    gg->support_valid = false;
-    int64_t T = 0;
-    TC_TRY(tc::compute_support(gg, gg->support, true, triangles_out ? &T : nullptr, s));
-    gg->support_valid = true;
-    if (triangles_out) {
-        gg->triangles = T;
-        *triangles_out = T;
+    // computed once per graph and kept (the peel starts from them too); a
+    // kernel forced by the test hook is always run
+    const bool need_T = triangles_out && gg->triangles < 0;
+    if (!gg->support_valid || need_T || tc::intersect_mode() != 0) {
+        if (!gg->support) TC_TRY(tc::dev_alloc_n(&gg->support, gg->m, s));
+        gg->support_valid = false;
+        int64_t T = 0;
+        // without triangles_out the call stays asynchronous (T not read back)
+        TC_TRY(tc::compute_support(gg, gg->support, true, triangles_out ? &T : nullptr, s));
+        if (triangles_out) gg->triangles = T;
+        gg->support_valid = true;
     }
+    if (triangles_out) *triangles_out = gg->triangles;
     // the cached supports are in internal edge order: scatter to edge ids
     if (gg->m == 0) return TC_OK;
     if (!tc::is_host_pointer(support_out))

@@ -508,3 +508,33 @@ def test_ktruss_components_without_edges():
     el, vl, c = tc.ktruss_components(g, 3)
     assert c == 0 and len(el) == 0 and (vl.cpu().numpy() == -1).all()
     tc.tc_graph_free(g)
+
+
+def test_support_without_count_then_peel_and_count():
+    """tc_edge_support without triangles_out (asynchronous) leaves T unknown;
+    a later peel and tc_count must still size and report everything from the
+    true T, and repeated calls reuse the graph's supports."""
+    src, dst, n = graphgen.rmat(11, seed=13)
+    og = oracle.OracleGraph.from_edges(src, dst, n)
+    g = tc.tc_build_csr(dev(src), dev(dst), n)
+    s1, none = tc.tc_edge_support(g, triangles=False)
+    assert none is None
+    assert np.array_equal(s1.cpu().numpy(), og.support())
+    for name, mode in PEEL_MODES.items():
+        prev = tc.tc_debug_peel_mode(mode)
+        try:
+            kmax, truss = tc.ktruss_max(g)
+        finally:
+            tc.tc_debug_peel_mode(prev)
+        want_kmax, want_truss = og.truss_decomposition()
+        assert kmax == want_kmax and np.array_equal(truss.cpu().numpy(), want_truss), name
+    assert tc.tc_count(g) == og.count()
+    s2, T2 = tc.tc_edge_support(g)
+    assert T2 == og.count() and np.array_equal(s2.cpu().numpy(), og.support())
+    tc.tc_graph_free(g)
+    # count first, then support: the support call knows T already
+    g = tc.tc_build_csr(dev(src), dev(dst), n)
+    assert tc.tc_count(g) == og.count()
+    s3, T3 = tc.tc_edge_support(g)
+    assert T3 == og.count() and np.array_equal(s3.cpu().numpy(), og.support())
+    tc.tc_graph_free(g)
