@@ -132,6 +132,9 @@ int ktruss(tc_graph* g, int32_t k, uint8_t* mask_out, int64_t* edges_out, void* 
  * graph has edges but no triangle, 0 if it has no edge).
  * truss_out: m int32 in edge-id order (device or host), the largest k whose
  * k-truss contains the edge (>= 2); may be NULL.
+ * The decomposition stays with the graph when it fits its optional memory
+ * (tc_graph_set_memory_limit; 4 bytes per edge): later ktruss_max calls copy
+ * it, and ktruss(k) becomes the threshold truss >= k (the k-trusses nest).
  * Synchronises the stream.
  */
 int ktruss_max(tc_graph* g, int32_t* kmax_out, int32_t* truss_out, void* cuda_stream);
@@ -162,7 +165,8 @@ typedef struct {
                               (the list entries a merge-based masked product
                               reads), or -1 until tc_graph_wedge_work ran */
     int64_t device_bytes;  /* device memory held by the graph (CSR, edge arrays,
-                              cached supports and cached triangle lists) */
+                              and what it keeps between calls: supports,
+                              triangle lists, the latest k-truss, truss numbers) */
     int64_t peel_rounds;   /* bulk removal rounds of the most recent ktruss /
                               ktruss_max call on this graph (0 if none) */
     int64_t peel_lists;    /* 1 if that call read precomputed per-edge triangle
@@ -186,6 +190,9 @@ typedef struct {
     int64_t peel_searches;
     int64_t peel_lookups;
     int64_t peel_lowered;
+    int64_t truss_cached;  /* 1 if the graph keeps the truss decomposition of
+                              its latest ktruss_max (later ktruss calls then
+                              threshold it instead of peeling) */
 } tc_graph_info_t;
 
 /* Fills *info (host pointer) from values the library already holds; launches
@@ -249,6 +256,87 @@ int ktruss_components(tc_graph* g, int32_t k, int32_t* edge_label_out, int32_t* 
  */
 int tc_read_edges(const char* path, int format, int32_t* src, int32_t* dst, int64_t capacity,
                   int64_t* m_out, int32_t* n_out);
+
+/*
+ * Serving (a request loop over device-resident graphs).  The paper times
+ * single kernels; this runs them as a service: requests for the triangle
+ * count or the k-truss size of one graph of a pool arrive over time and are
+ * served by `slots` worker threads, each with its own CUDA stream, with
+ * continuous batching: a free slot takes the oldest request that can run
+ * now (its graph idle — a graph serves one call at a time — and resident,
+ * or admissible within the device-memory budget after evicting
+ * least-recently-used idle graphs), so requests that arrive while others
+ * run overlap on the device.  Graphs are built on first use from the
+ * caller's host edge lists (tc_build_csr rules) and get a memory bound of
+ * optional_bytes_per_pair x input pairs (tc_graph_set_memory_limit); a
+ * graph's first k-truss request computes its truss decomposition, which it
+ * keeps, so later k-truss requests on it threshold the truss numbers.
+ */
+typedef struct {
+    const int32_t* src;  /* host, m_in entries; must stay valid while the server lives */
+    const int32_t* dst;
+    int64_t m_in;
+    int32_t n;
+    int32_t pad;
+} tc_graph_source;
+
+#define TC_REQ_COUNT 0   /* result: the graph's triangle count */
+#define TC_REQ_KTRUSS 1  /* result: edges in the graph's k-truss (k >= 2) */
+
+typedef struct {
+    int32_t graph;     /* index into the sources */
+    int32_t kind;      /* TC_REQ_COUNT or TC_REQ_KTRUSS */
+    int32_t k;
+    int32_t pad;
+    double arrival_s;  /* seconds after the run starts (open loop); non-decreasing */
+} tc_request;
+
+typedef struct {
+    int64_t result;
+    double start_s;    /* when a slot took the request (seconds after the run start) */
+    double done_s;     /* when its result was on the host */
+    int32_t status;    /* TC_* of the request */
+    int32_t slot;
+} tc_response;
+
+typedef struct {
+    int64_t builds, evictions, max_concurrent, peak_reserved_bytes, errors;
+    int64_t violations;        /* test hook only: concurrent calls seen on one graph */
+    int64_t reserved_bytes;    /* device bytes reserved for resident graphs now */
+    int64_t resident_graphs;
+} tc_server_stats;
+
+typedef struct tc_server tc_server;
+
+/* Creates a server on the current device (graphs are built later, on first
+ * use).  budget_bytes: device memory for resident graphs.  slots: 1..256.
+ * Errors: TC_EINVAL (NULL, bad sizes, a bad source), TC_ECUDA, TC_ENOMEM. */
+int tc_server_create(const tc_graph_source* sources, int32_t num_graphs, int64_t budget_bytes,
+                     int64_t optional_bytes_per_pair, int32_t slots, tc_server** out);
+
+/* Serves num_reqs requests and returns when all are done.  open_loop = 1:
+ * a request becomes available at its arrival_s; 0: all at once (closed
+ * loop).  slots: how many of the server's slots serve this run (0 = all;
+ * 1 = the plain loop, one request at a time in order, on the same resident
+ * graphs).  out[i] receives request i's result, times, status and slot;
+ * *wall_s (may be NULL) the run's duration.  Latency of request i =
+ * out[i].done_s - reqs[i].arrival_s.  Graphs stay resident between runs.
+ * Returns TC_OK, or TC_ECUDA if any request failed (its status says how),
+ * TC_ERANGE / TC_EINVAL for a request naming no graph or malformed. */
+int tc_server_run(tc_server* srv, const tc_request* reqs, int64_t num_reqs, int32_t open_loop,
+                  int32_t slots, tc_response* out, double* wall_s);
+
+/* Counters of the server's life so far (host struct).  Launches nothing. */
+int tc_server_get_stats(const tc_server* srv, tc_server_stats* out);
+
+/* Frees the server's graphs and streams.  NULL is a no-op. */
+void tc_server_destroy(tc_server* srv);
+
+/* Test hook: servers created while this is on run their scheduler with
+ * sleeps in place of device work (no CUDA calls; results are
+ * graph * 1000 + k), so the host logic can be tested without a GPU.
+ * Returns the previous setting. */
+int tc_debug_server_fake(int on);
 
 /* Number of CUDA kernels the library has launched in this process (all
  * graphs, all threads); lets a caller count the launches of a region. */

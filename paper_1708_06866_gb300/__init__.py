@@ -30,7 +30,8 @@ __all__ = [
     "TCError", "Graph", "load_library", "library_path", "tc_build_csr", "tc_count",
     "tc_edge_support", "ktruss", "ktruss_max", "ktruss_components", "tc_num_edges", "tc_num_vertices", "tc_edges",
     "tc_graph_info", "tc_graph_wedge_work", "tc_launch_count", "tc_batch_run",
-    "tc_graph_set_memory_limit", "tc_read_edges",
+    "tc_graph_set_memory_limit", "tc_read_edges", "tc_debug_server_fake", "GraphSource",
+    "ServeRequest", "ServeResponse", "ServerStats", "TC_REQ_COUNT", "TC_REQ_KTRUSS",
     "tc_graph_free", "tc_strerror", "tc_last_error", "tc_debug_fail_alloc",
     "tc_debug_spin_limit_ns", "tc_debug_peel_mode", "tc_debug_intersect_mode", "TC_OK", "TC_EINVAL", "TC_ERANGE", "TC_ENOMEM", "TC_ECUDA",
     "TC_ETIMEDOUT", "TC_EOVERFLOW", "TC_INPUT_AUTO", "TC_INPUT_DEVICE", "TC_INPUT_HOST",
@@ -78,6 +79,14 @@ def load_library(build_if_missing: bool = True):
             "ktruss_components": (ctypes.c_int, [vp, i32, vp, vp, ctypes.POINTER(i64), vp]),
             "tc_read_edges": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, vp, vp, i64,
                                              ctypes.POINTER(i64), ctypes.POINTER(i32)]),
+            "tc_server_create": (ctypes.c_int, [ctypes.POINTER(GraphSource), i32, i64, i64,
+                                                i32, ctypes.POINTER(vp)]),
+            "tc_server_run": (ctypes.c_int, [vp, ctypes.POINTER(ServeRequest), i64, i32, i32,
+                                             ctypes.POINTER(ServeResponse),
+                                             ctypes.POINTER(ctypes.c_double)]),
+            "tc_server_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(ServerStats)]),
+            "tc_server_destroy": (None, [vp]),
+            "tc_debug_server_fake": (ctypes.c_int, [ctypes.c_int]),
             "tc_batch_run": (ctypes.c_int, [ctypes.POINTER(BatchDesc), vp]),
             "tc_graph_wedge_work": (ctypes.c_int, [vp, ctypes.POINTER(i64), vp]),
             "tc_debug_fail_alloc": (i64, [i64]),
@@ -93,13 +102,42 @@ def load_library(build_if_missing: bool = True):
         return lib
 
 
+class GraphSource(ctypes.Structure):
+    """Mirror of tc_graph_source."""
+    _fields_ = [("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("m_in", ctypes.c_int64),
+                ("n", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class ServeRequest(ctypes.Structure):
+    """Mirror of tc_request."""
+    _fields_ = [("graph", ctypes.c_int32), ("kind", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("arrival_s", ctypes.c_double)]
+
+
+class ServeResponse(ctypes.Structure):
+    """Mirror of tc_response."""
+    _fields_ = [("result", ctypes.c_int64), ("start_s", ctypes.c_double),
+                ("done_s", ctypes.c_double), ("status", ctypes.c_int32), ("slot", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    """Mirror of tc_server_stats."""
+    _fields_ = [(f, ctypes.c_int64) for f in
+                ("builds", "evictions", "max_concurrent", "peak_reserved_bytes", "errors",
+                 "violations", "reserved_bytes", "resident_graphs")]
+
+
+TC_REQ_COUNT, TC_REQ_KTRUSS = 0, 1
+
+
 class GraphInfo(ctypes.Structure):
     """Mirror of tc_graph_info_t."""
     _fields_ = [(f, ctypes.c_int64) for f in
                 ("n", "m_in", "m", "max_degree", "max_out", "wedge_work", "device_bytes",
                  "peel_rounds", "peel_lists", "count_kernel_ns", "support_kernel_ns",
                  "lists_kernel_ns", "peel_kernel_ns", "peel_bytes", "peel_scanned",
-                 "peel_entries", "peel_searches", "peel_lookups", "peel_lowered")]
+                 "peel_entries", "peel_searches", "peel_lookups", "peel_lowered",
+                 "truss_cached")]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -393,6 +431,11 @@ def tc_graph_free(g: Graph):
 
 def tc_debug_fail_alloc(nth: int) -> int:
     return int(load_library().tc_debug_fail_alloc(int(nth)))
+
+
+def tc_debug_server_fake(on: bool) -> bool:
+    """Test hook: servers created while on sleep instead of using the GPU."""
+    return bool(load_library().tc_debug_server_fake(1 if on else 0))
 
 
 def tc_debug_peel_mode(mode: int) -> int:

@@ -46,6 +46,9 @@ constexpr int64_t HEAVY = 4096;  // triangle-list length above which an edge is 
 #endif
 constexpr int64_t LANE_EDGES = TC_PK_LANE_EDGES;
 constexpr int64_t SHORT_LIST = TC_PK_SHORT_LIST;
+#ifndef TC_PK_MAX_BLOCKS
+#define TC_PK_MAX_BLOCKS (1 << 20)   // cap on the peel's grid
+#endif
 #ifndef TC_PK_UNROLL
 #define TC_PK_UNROLL 2               // triangle-list entries per lane in flight
 #endif
@@ -774,9 +777,11 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
     int per_sm = 0;
     TC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p.fn, PK_THREADS, 0));
     if (per_sm < 1) return fail(TC_ECUDA, "k_peel cannot be resident");
-    // small graphs get a smaller grid (cheaper barriers, and room for other
-    // streams' work); large ones fill every SM twice
-    const int64_t want = std::max<int64_t>(1, (m + 8191) / 8192);
+    // one block per ~24K edges up to one per SM: the peel is latency-bound,
+    // so below about 4M edges a partial grid is as fast (cheaper barriers)
+    // and leaves SMs to other streams' work (concurrent requests)
+    const int64_t want = std::min<int64_t>(std::max<int64_t>(1, (m + 24575) / 24576),
+                                           TC_PK_MAX_BLOCKS);
     p.blocks = (int)std::min<int64_t>(want, (int64_t)num_sms() * std::min(per_sm, 1024 / PK_THREADS));
     g->last_peel_lists = p.tl;
     return TC_OK;
@@ -893,10 +898,44 @@ int mask_from_state(const int32_t* t, const int32_t* fwd, int64_t m, uint8_t* ma
     return TC_OK;
 }
 
+namespace {
+// The k-truss from truss numbers: e is in it iff truss[e] >= k (the
+// k-trusses nest, Section III-B); counts the edges in it.
+__global__ void k_mask_from_truss(const int32_t* __restrict__ truss, int64_t m, int32_t k,
+                                  uint8_t* __restrict__ mask,
+                                  unsigned long long* __restrict__ count) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long c = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const bool in = truss[e] >= k;
+        mask[e] = in ? 1 : 0;
+        c += in;
+    }
+    c = warp_sum(c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+// A test hook forcing a peel form always peels.
+bool truss_cache_usable(const Graph* g) {
+    return g->truss_valid && peel_mode() == PEEL_AUTO && intersect_mode() == 0;
+}
+}  // namespace
+
 int peel_ktruss(Graph* g, int32_t k, uint8_t* mask, int64_t* edges_left, cudaStream_t s) {
     const int64_t m = g->m;
     if (m == 0) {
         if (edges_left) *edges_left = 0;
+        return TC_OK;
+    }
+    if (truss_cache_usable(g)) {
+        unsigned long long* cnt = g->dev_scalars + 1;
+        TC_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+        k_mask_from_truss<<<small_grid(m), 256, 0, s>>>(g->truss_cache, m, k, mask, cnt);
+        TC_LAUNCH_CHECK("k_mask_from_truss");
+        unsigned long long h = 0;
+        TC_CUDA_TRY(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
+        TC_CUDA_TRY(cudaStreamSynchronize(s));
+        if (edges_left) *edges_left = (int64_t)h;
         return TC_OK;
     }
     PeelCtl r{};
@@ -906,13 +945,35 @@ int peel_ktruss(Graph* g, int32_t k, uint8_t* mask, int64_t* edges_left, cudaStr
 }
 
 int peel_decompose(Graph* g, int32_t* truss, int32_t* kmax, cudaStream_t s) {
-    if (g->m == 0) {
+    const int64_t m = g->m;
+    if (m == 0) {
         *kmax = 0;
+        return TC_OK;
+    }
+    if (truss_cache_usable(g)) {
+        TC_CUDA_TRY(cudaMemcpyAsync(truss, g->truss_cache, sizeof(int32_t) * m,
+                                    cudaMemcpyDeviceToDevice, s));
+        *kmax = g->truss_kmax;
         return TC_OK;
     }
     PeelCtl r{};
     TC_TRY(run_peel(g, 3, false, nullptr, truss, &r, s));
     *kmax = r.kmax;
+    // keep the decomposition when it fits the graph's optional memory
+    const double bytes = 4.0 * (double)m;
+    bool room = g->truss_cache != nullptr;
+    if (!room) {
+        size_t free_b = 0, total_b = 0;
+        TC_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        room = g->mem_limit >= 0 ? bytes <= (double)g->mem_limit : bytes < 0.4 * (double)free_b;
+        if (room) TC_TRY(dev_alloc_n(&g->truss_cache, m, s));
+    }
+    if (room) {
+        TC_CUDA_TRY(cudaMemcpyAsync(g->truss_cache, truss, sizeof(int32_t) * m,
+                                    cudaMemcpyDeviceToDevice, s));
+        g->truss_kmax = r.kmax;
+        g->truss_valid = true;
+    }
     return TC_OK;
 }
 

@@ -113,6 +113,7 @@ void free_graph(Graph* g) {
     dev_free(g->support, s);
     dev_free(g->tri_off, s);
     dev_free(g->tri_pairs, s);
+    dev_free(g->truss_cache, s);
     dev_free(g->kt_state, s);
     dev_free(g->kt_support, s);
     dev_free(g->kt_col, s);
@@ -227,7 +228,7 @@ int tc_count(tc_graph* g, int64_t* triangles_out, void* cuda_stream) {
     DeviceGuard dg(g->g.device);
     // the graph is immutable: once its supports are computed, T is known
     // (a kernel forced by the test hook is always run)
-    if (g->g.support_valid && g->g.triangles >= 0 && tc::intersect_mode() == 0) {
+    if (g->g.triangles >= 0 && tc::intersect_mode() == 0) {
         *triangles_out = g->g.triangles;
         return TC_OK;
     }
@@ -355,7 +356,7 @@ int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream) {
     info->device_bytes = m * (4 + 4 + 8 + 4 + 4 + 4) + 8 * (n + 1) + 8 * n +
                          (gg->support ? 4 * m : 0) +
                          (gg->tri_valid ? 8 * (m + 1) + 24 * gg->triangles : 0) +
-                         (gg->kt_state ? 8 * m : 0) + (gg->kt_col ? 16 * m + 4 * n : 0);
+                         (gg->kt_state ? 8 * m : 0) + (gg->truss_cache ? 4 * m : 0) + (gg->kt_col ? 16 * m + 4 * n : 0);
     info->peel_rounds = gg->last_peel_rounds;
     info->peel_lists = gg->last_peel_lists ? 1 : 0;
     info->count_kernel_ns = gg->stats.count_ns;
@@ -368,6 +369,7 @@ int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream) {
     info->peel_searches = gg->stats.peel_searches;
     info->peel_lookups = gg->stats.peel_lookups;
     info->peel_lowered = gg->stats.peel_lowered;
+    info->truss_cached = gg->truss_valid ? 1 : 0;
     return TC_OK;
 }
 

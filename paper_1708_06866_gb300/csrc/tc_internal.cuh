@@ -258,6 +258,11 @@ struct Graph {
     int32_t* kt_eid = nullptr;
     int32_t* kt_rowlen = nullptr;
     bool kt_adj = false;
+    // the truss decomposition of the latest ktruss_max (canonical order),
+    // kept when it fits: later ktruss calls threshold it instead of peeling
+    int32_t* truss_cache = nullptr;
+    int32_t truss_kmax = 0;
+    bool truss_valid = false;
     // bound on optional device memory for this graph (triangle lists, their
     // cache, the cached compacted adjacency); -1 = a share of free memory
     int64_t mem_limit = -1;

@@ -1,28 +1,27 @@
-"""Serving loop: triangle-count and k-truss queries on device-resident graphs.
+"""Serving: triangle-count and k-truss queries on device-resident graphs.
 
-Requests (graph id, query) arrive over time and are served with continuous
-batching: a fixed number of worker slots, each with its own CUDA stream,
-take the oldest admissible request as soon as they are free, so work of
-requests that arrive while others run overlaps on the device.  Graphs are
-built on first use and kept resident (their CSR and cached supports) under
-an HBM budget; least-recently-used idle graphs are evicted to admit a new
-one, and a request whose graph cannot be admitted yet waits while requests
-on resident graphs go ahead.  A graph serves one call at a time (the ABI's
-rule); requests for different graphs overlap.
+A thin wrapper over the library's native request loop (``tc_server_*`` in
+``include/tc.h``): requests (graph id, query) arrive over time and are
+served with continuous batching by a fixed number of worker threads, each
+with its own CUDA stream; a free slot takes the oldest request whose graph
+is idle and resident, or can be made resident within the device-memory
+budget after evicting least-recently-used idle graphs.  Graphs are built on
+first use and kept resident; a graph serves one call at a time, requests for
+different graphs overlap.  Latency runs from a request's arrival to its
+result on the host.
 
-The scheduler talks to a backend (build / free / query); ``GpuBackend`` runs
-the library's kernels.  Latency is measured on the host from a request's
-arrival to its result.
+This module only marshals: traces in, results out.  It also generates
+Poisson traces and summarises latencies.
 """
 from __future__ import annotations
 
-import collections
+import ctypes
 import dataclasses
-import threading
-import time
-from typing import Callable, Dict, List, Optional
+from typing import Dict, List, Optional
 
 import numpy as np
+
+import paper_1708_06866_gb300 as tc
 
 
 @dataclasses.dataclass
@@ -31,216 +30,99 @@ class Request:
     graph: int
     kind: str             # "count" or "ktruss"
     k: int = 0
-    arrival: float = 0.0  # host clock (time.perf_counter) at submission
+    arrival: float = 0.0  # seconds after the run start
     start: float = 0.0
     done: float = 0.0
     result: Optional[int] = None
     error: Optional[str] = None
     slot: int = -1
-    event: threading.Event = dataclasses.field(default_factory=threading.Event)
 
     @property
     def latency(self) -> float:
         return self.done - self.arrival
 
 
-class GpuBackend:
-    """Builds graphs with tc_build_csr and answers queries with tc_count /
-    ktruss on the caller's stream.  Graph inputs stay on the host until
-    built (the build copies them in)."""
+class NativeServer:
+    """The library's server over a pool of graphs {id: (src, dst, n)} with
+    host int32 edge lists (kept referenced while the server lives)."""
 
-    def __init__(self, graphs: Dict[int, tuple], device: int = 0):
-        import torch
-        import paper_1708_06866_gb300 as tc
-        self.tc = tc
-        self.torch = torch
-        self.graphs = graphs
-        self.device = device
-        torch.cuda.set_device(device)
-
-    def new_stream(self):
-        return self.torch.cuda.Stream(device=self.device)
-
-    # per input pair: CSR and edge arrays (~40 B), call scratch of a peel
-    # (~60 B), and the optional memory (triangle lists, caches) the graph may
-    # use (OPTIONAL_PER_PAIR, enforced through tc_graph_set_memory_limit)
-    OPTIONAL_PER_PAIR = 40
-
-    def estimate_bytes(self, gid: int) -> int:
-        """Device bytes a graph may need while it is used."""
-        src, _, _ = self.graphs[gid]
-        return (100 + self.OPTIONAL_PER_PAIR) * len(src) + (1 << 20)
-
-    def build(self, gid: int, stream):
-        src, dst, n = self.graphs[gid]
-        with self.torch.cuda.stream(stream):
-            g = self.tc.tc_build_csr(src, dst, n, stream=stream)
-        self.tc.tc_graph_set_memory_limit(g, self.OPTIONAL_PER_PAIR * len(src))
-        return g
-
-    def free(self, handle):
-        handle.free()
-
-    def held_bytes(self, handle) -> int:
-        """Device bytes the graph holds now (it keeps supports and triangle
-        lists between queries)."""
-        return int(self.tc.tc_graph_info(handle)["device_bytes"])
-
-    def query(self, handle, req: Request, stream) -> int:
-        with self.torch.cuda.stream(stream):
-            if req.kind == "count":
-                return self.tc.tc_count(handle, stream=stream)
-            _, left = self.tc.ktruss(handle, req.k, stream=stream)
-            return left
-
-
-class Server:
-    """Continuous-batching scheduler over a backend."""
-
-    def __init__(self, backend, slots: int = 8, budget_bytes: int = 120 << 30):
-        self.backend = backend
+    def __init__(self, pool: Dict[int, tuple], slots: int = 8, budget_bytes: int = 120 << 30,
+                 optional_bytes_per_pair: int = 40):
+        self.lib = tc.load_library()
+        self.handle = None
+        self.ids = sorted(pool)
+        self.index = {g: i for i, g in enumerate(self.ids)}
+        self._keep = []
+        src = (tc.GraphSource * max(1, len(self.ids)))()
+        for i, g in enumerate(self.ids):
+            s, d, n = pool[g]
+            s = np.ascontiguousarray(s, dtype=np.int32)
+            d = np.ascontiguousarray(d, dtype=np.int32)
+            self._keep += [s, d]
+            src[i].src = s.ctypes.data or None
+            src[i].dst = d.ctypes.data or None
+            src[i].m_in = len(s)
+            src[i].n = int(n)
+        self._src = src
+        self.m_in = {g: int(pool[g][0].shape[0]) for g in self.ids}
+        h = ctypes.c_void_p()
+        tc._check(self.lib.tc_server_create(src, len(self.ids), int(budget_bytes),
+                                            int(optional_bytes_per_pair), int(slots),
+                                            ctypes.byref(h)), "tc_server_create")
+        self.handle = h.value
         self.slots = slots
-        self.budget = budget_bytes
-        self.cv = threading.Condition()
-        self.pending: collections.deque = collections.deque()
-        self.resident: "collections.OrderedDict[int, dict]" = collections.OrderedDict()
-        self.reserved = 0
-        self.busy_graphs = set()
-        self.building = set()
-        self.stop = False
-        self.completed: List[Request] = []
-        self.evictions = 0
-        self.builds = 0
-        self.max_concurrent = 0
-        self.running = 0
-        self.threads = [threading.Thread(target=self._worker, args=(i,), daemon=True)
-                        for i in range(slots)]
-        for t in self.threads:
-            t.start()
 
-    # ---------------------------------------------------------- client side
-    def submit(self, req: Request) -> Request:
-        req.arrival = time.perf_counter()
-        with self.cv:
-            self.pending.append(req)
-            self.cv.notify_all()
-        return req
+    def run(self, trace, open_loop: bool = True, slots: int = 0) -> float:
+        """Serves [(arrival seconds, Request)] in order; fills each Request's
+        result, times, slot and error.  slots: how many of the server's slots
+        serve (0 = all; 1 = the plain one-at-a-time loop).  Returns the run's
+        wall time (s)."""
+        n = len(trace)
+        reqs = (tc.ServeRequest * max(1, n))()
+        for i, (at, r) in enumerate(trace):
+            reqs[i].graph = self.index[r.graph]
+            reqs[i].kind = tc.TC_REQ_COUNT if r.kind == "count" else tc.TC_REQ_KTRUSS
+            reqs[i].k = int(r.k)
+            reqs[i].arrival_s = float(at) if open_loop else 0.0
+        out = (tc.ServeResponse * max(1, n))()
+        wall = ctypes.c_double()
+        rc = self.lib.tc_server_run(self.handle, reqs, n, 1 if open_loop else 0, int(slots), out,
+                                    ctypes.byref(wall))
+        if rc not in (tc.TC_OK, tc.TC_ECUDA):
+            tc._check(rc, "tc_server_run")
+        for i, (at, r) in enumerate(trace):
+            o = out[i]
+            r.arrival = float(at) if open_loop else 0.0
+            r.start, r.done, r.slot = o.start_s, o.done_s, o.slot
+            if o.status == tc.TC_OK:
+                r.result, r.error = int(o.result), None
+            else:
+                r.result, r.error = None, f"{tc.tc_strerror(o.status)} (code {o.status})"
+        return wall.value
 
-    def shutdown(self):
-        with self.cv:
-            self.stop = True
-            self.cv.notify_all()
-        for t in self.threads:
-            t.join(timeout=60)
-        for gid, ent in list(self.resident.items()):
-            if ent["handle"] is not None:
-                self.backend.free(ent["handle"])
-        self.resident.clear()
+    def stats(self) -> dict:
+        st = tc.ServerStats()
+        tc._check(self.lib.tc_server_get_stats(self.handle, ctypes.byref(st)),
+                  "tc_server_get_stats")
+        return {f: int(getattr(st, f)) for f, _ in st._fields_}
 
-    # ---------------------------------------------------------- scheduling
-    def _admissible(self, req: Request) -> bool:
-        """The graph is resident and idle, or can be made resident (budget
-        after evicting idle graphs) and nobody is building it."""
-        g = req.graph
-        if g in self.busy_graphs or g in self.building:
-            return False
-        if g in self.resident:
-            return True
-        need = self.backend.estimate_bytes(g)
-        freeable = sum(e["bytes"] for gid, e in self.resident.items()
-                       if gid not in self.busy_graphs)
-        return self.reserved - freeable + need <= self.budget or not self.resident
+    def close(self):
+        if self.handle:
+            self.lib.tc_server_destroy(self.handle)
+            self.handle = None
 
-    def _take(self) -> Optional[Request]:
-        """Oldest admissible request (FIFO among those that can run now)."""
-        for i, req in enumerate(self.pending):
-            if self._admissible(req):
-                del self.pending[i]
-                return req
-        return None
-
-    def _make_room(self, need: int) -> List:
-        """Evicts least-recently-used idle graphs until `need` fits; returns
-        their handles for freeing outside the lock."""
-        out = []
-        for gid in list(self.resident.keys()):
-            if self.reserved + need <= self.budget:
-                break
-            if gid in self.busy_graphs:
-                continue
-            ent = self.resident.pop(gid)
-            self.reserved -= ent["bytes"]
-            self.evictions += 1
-            out.append(ent["handle"])
-        return out
-
-    def _worker(self, slot: int):
-        stream = self.backend.new_stream()
-        while True:
-            with self.cv:
-                req = None
-                while not self.stop:
-                    req = self._take()
-                    if req is not None:
-                        break
-                    self.cv.wait(timeout=0.05)
-                if req is None:
-                    return
-                g = req.graph
-                self.busy_graphs.add(g)
-                handle = None
-                to_free = []
-                if g in self.resident:
-                    self.resident.move_to_end(g)
-                    handle = self.resident[g]["handle"]
-                else:
-                    need = self.backend.estimate_bytes(g)
-                    to_free = self._make_room(need)
-                    self.reserved += need
-                    self.building.add(g)
-                self.running += 1
-                self.max_concurrent = max(self.max_concurrent, self.running)
-            for h in to_free:
-                self.backend.free(h)
-            req.slot = slot
-            req.start = time.perf_counter()
-            try:
-                if handle is None:
-                    handle = self.backend.build(g, stream)
-                    with self.cv:
-                        self.builds += 1
-                        self.building.discard(g)
-                        self.resident[g] = {"handle": handle,
-                                            "bytes": self.backend.estimate_bytes(g)}
-                req.result = self.backend.query(handle, req, stream)
-                held = getattr(self.backend, "held_bytes", None)
-                if held is not None:
-                    now_bytes = max(held(handle), self.backend.estimate_bytes(g))
-                    with self.cv:
-                        ent = self.resident.get(g)
-                        if ent is not None and now_bytes != ent["bytes"]:
-                            self.reserved += now_bytes - ent["bytes"]
-                            ent["bytes"] = now_bytes
-            except Exception as exc:  # reported per request, the server keeps going
-                req.error = repr(exc)
-                with self.cv:
-                    if g in self.building:
-                        self.building.discard(g)
-                        self.reserved -= self.backend.estimate_bytes(g)
-            req.done = time.perf_counter()
-            with self.cv:
-                self.busy_graphs.discard(g)
-                self.running -= 1
-                self.completed.append(req)
-                self.cv.notify_all()
-            req.event.set()
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def poisson_trace(num: int, rate: float, graph_ids, seed: int, ks=(3, 4, 5, 6, 7, 8),
                   count_share: float = 0.5):
-    """Requests with exponential inter-arrival gaps (rate per second): half
-    triangle counts, half k-truss queries with k uniform in ks, on graphs
-    drawn uniformly from graph_ids."""
+    """Requests with exponential inter-arrival gaps (rate per second; 0 = all
+    at once): half triangle counts, half k-truss queries with k uniform in
+    ks, on graphs drawn uniformly from graph_ids."""
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate, num) if rate > 0 else np.zeros(num)
     times = np.cumsum(gaps) - gaps[0]
@@ -251,20 +133,9 @@ def poisson_trace(num: int, rate: float, graph_ids, seed: int, ks=(3, 4, 5, 6, 7
                                       0 if is_count[i] else int(kk[i]))) for i in range(num)]
 
 
-def replay(server: Server, trace, timeout: float = 600.0,
-           clock: Callable[[], float] = time.perf_counter):
-    """Submits each request at its scheduled offset and waits for all."""
-    t0 = clock()
-    for at, req in trace:
-        delay = at - (clock() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        server.submit(req)
-    deadline = time.perf_counter() + timeout
-    for _, req in trace:
-        if not req.event.wait(max(0.0, deadline - time.perf_counter())):
-            raise TimeoutError(f"request {req.rid} not served in time")
-    return clock() - t0
+def fresh(trace):
+    """The same requests, unserved (for another run)."""
+    return [(at, Request(r.rid, r.graph, r.kind, r.k)) for at, r in trace]
 
 
 def summarize(reqs: List[Request], wall: float) -> dict:

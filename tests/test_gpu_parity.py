@@ -538,3 +538,33 @@ def test_support_without_count_then_peel_and_count():
     s3, T3 = tc.tc_edge_support(g)
     assert T3 == og.count() and np.array_equal(s3.cpu().numpy(), og.support())
     tc.tc_graph_free(g)
+
+
+def test_kept_decomposition_answers_ktruss():
+    """After ktruss_max the graph keeps its truss numbers; ktruss(k) for any
+    k, ktruss_components and a second ktruss_max are answered from them and
+    equal the oracle's peel."""
+    src, dst, n = graphgen.rmat(12, seed=17)
+    og = oracle.OracleGraph.from_edges(src, dst, n)
+    want_kmax, want_truss = og.truss_decomposition()
+    g = tc.tc_build_csr(dev(src), dev(dst), n)
+    assert tc.tc_graph_info(g)["truss_cached"] == 0
+    kmax, truss = tc.ktruss_max(g)
+    assert kmax == want_kmax and np.array_equal(truss.cpu().numpy(), want_truss)
+    assert tc.tc_graph_info(g)["truss_cached"] == 1
+    for k in range(2, want_kmax + 2):
+        mask, sup, left = og.ktruss(k)
+        mk, c = tc.ktruss(g, k)
+        assert c == left and np.array_equal(mk.cpu().numpy(), mask), k
+        el, vl, cc = tc.ktruss_components(g, k)
+        wel, wvl, wc = og.ktruss_components(k)
+        assert cc == wc and np.array_equal(el.cpu().numpy(), wel), k
+    kmax2, truss2 = tc.ktruss_max(g)
+    assert kmax2 == want_kmax and np.array_equal(truss2.cpu().numpy(), want_truss)
+    # a zero memory bound leaves nothing kept on a fresh graph
+    g2 = tc.tc_build_csr(dev(src), dev(dst), n)
+    tc.tc_graph_set_memory_limit(g2, 0)
+    tc.ktruss_max(g2)
+    assert tc.tc_graph_info(g2)["truss_cached"] == 0
+    tc.tc_graph_free(g2)
+    tc.tc_graph_free(g)

@@ -1,6 +1,8 @@
-"""Serving on the GPU: results of requests served concurrently (several
-slots, overlapping streams, resident graphs) equal the results of the same
-queries made one at a time, and the oracle's."""
+"""Serving on the GPU through the native server: results of requests served
+concurrently (several slots, overlapping streams, resident graphs, kept
+truss decompositions) equal the results of the same queries made one at a
+time, and the oracle's; a small budget forces evictions and rebuilds with
+the same results."""
 import numpy as np
 import pytest
 
@@ -17,27 +19,34 @@ import paper_1708_06866_gb300 as tc  # noqa: E402
 from paper_1708_06866_gb300 import serve  # noqa: E402
 
 
-def test_results_alone_equal_results_in_the_mix():
-    pool = graphgen.rmat_pool(8, seed=11, n_min=1 << 8, n_max=1 << 13)
-    backend = serve.GpuBackend(pool)
-    srv = serve.Server(backend, slots=6, budget_bytes=8 << 30)
-    trace = serve.poisson_trace(160, rate=0, graph_ids=list(pool), seed=12)
-    serve.replay(srv, trace)
-    srv.shutdown()
-    reqs = [r for _, r in trace]
-    assert all(r.error is None for r in reqs), [r.error for r in reqs if r.error]
-    assert srv.max_concurrent >= 2
-    # alone: one graph, one call at a time, default stream
-    alone = {}
+def alone_results(pool):
+    """Every query answered alone: one graph, one call at a time, default stream."""
+    out = {}
     for gid, (s, d, n) in pool.items():
         g = tc.tc_build_csr(s, d, n)
-        alone[(gid, "count", 0)] = tc.tc_count(g)
+        out[(gid, "count", 0)] = tc.tc_count(g)
         for k in range(3, 9):
-            alone[(gid, "ktruss", k)] = tc.ktruss(g, k)[1]
+            out[(gid, "ktruss", k)] = tc.ktruss(g, k)[1]
         g.free()
+    return out
+
+
+def test_results_alone_equal_results_in_the_mix():
+    pool = graphgen.rmat_pool(8, seed=11, n_min=1 << 8, n_max=1 << 13)
+    srv = serve.NativeServer(pool, slots=6, budget_bytes=8 << 30)
+    trace = serve.poisson_trace(200, rate=0, graph_ids=list(pool), seed=12)
+    srv.run(trace, open_loop=False)
+    # and again open loop, on resident graphs with kept decompositions
+    trace2 = serve.poisson_trace(200, rate=5000.0, graph_ids=list(pool), seed=13)
+    srv.run(trace2)
+    st = srv.stats()
+    srv.close()
+    reqs = [r for _, r in trace + trace2]
+    assert all(r.error is None for r in reqs), [r.error for r in reqs if r.error]
+    assert st["max_concurrent"] >= 2 and st["errors"] == 0
+    alone = alone_results(pool)
     for r in reqs:
         assert r.result == alone[(r.graph, r.kind, r.k)], r
-    # and the oracle, on a few graphs
     for gid in list(pool)[:3]:
         s, d, n = pool[gid]
         og = oracle.OracleGraph.from_edges(s, d, n)
@@ -48,16 +57,13 @@ def test_results_alone_equal_results_in_the_mix():
 
 def test_budget_forces_eviction_and_rebuild_on_gpu():
     pool = graphgen.rmat_pool(6, seed=13, n_min=1 << 9, n_max=1 << 11)
-    backend = serve.GpuBackend(pool)
-    two = sorted(backend.estimate_bytes(g) for g in pool)[-2:]
-    srv = serve.Server(backend, slots=2, budget_bytes=sum(two))
-    trace = serve.poisson_trace(60, rate=0, graph_ids=list(pool), seed=14)
-    serve.replay(srv, trace)
-    srv.shutdown()
-    assert srv.evictions > 0
+    est = sorted(140 * len(pool[g][0]) + (1 << 20) for g in pool)
+    srv = serve.NativeServer(pool, slots=2, budget_bytes=sum(est[-2:]))
+    trace = serve.poisson_trace(80, rate=0, graph_ids=list(pool), seed=14)
+    srv.run(trace, open_loop=False)
+    st = srv.stats()
+    srv.close()
+    assert st["evictions"] > 0 and st["errors"] == 0
+    alone = alone_results(pool)
     for _, r in trace:
-        s, d, n = pool[r.graph]
-        g = tc.tc_build_csr(s, d, n)
-        want = tc.tc_count(g) if r.kind == "count" else tc.ktruss(g, r.k)[1]
-        g.free()
-        assert r.result == want
+        assert r.error is None and r.result == alone[(r.graph, r.kind, r.k)], r

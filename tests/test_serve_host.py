@@ -1,109 +1,87 @@
-"""The serving scheduler's host logic on CPU, with a fake backend: every
-request is served exactly once with its own result, a graph is never used
-by two calls at once, resident bytes stay within the budget (least-recently
-used idle graphs are evicted), and requests overlap."""
-import threading
-import time
-
+"""The native server's host logic on CPU (its test hook runs the scheduler
+with sleeps in place of device work, no CUDA calls): every request is
+served exactly once with its own result, a graph is never used by two calls
+at once, reserved bytes stay within the budget (least-recently-used idle
+graphs are evicted), requests overlap, none starts before it arrives, and
+malformed requests are refused."""
+import numpy as np
 import pytest
 
+import paper_1708_06866_gb300 as tc
 from paper_1708_06866_gb300 import serve
 
 
-class FakeBackend:
-    def __init__(self, sizes, delay=0.002):
-        self.sizes = sizes
-        self.delay = delay
-        self.lock = threading.Lock()
-        self.in_use = set()
-        self.resident_bytes = 0
-        self.peak_bytes = 0
-        self.violations = []
-
-    def new_stream(self):
-        return object()
-
-    def estimate_bytes(self, gid):
-        return self.sizes[gid]
-
-    def build(self, gid, stream):
-        with self.lock:
-            self.resident_bytes += self.sizes[gid]
-            self.peak_bytes = max(self.peak_bytes, self.resident_bytes)
-        time.sleep(self.delay)
-        return {"gid": gid}
-
-    def free(self, handle):
-        with self.lock:
-            self.resident_bytes -= self.sizes[handle["gid"]]
-
-    def query(self, handle, req, stream):
-        g = handle["gid"]
-        with self.lock:
-            if g in self.in_use:
-                self.violations.append(g)
-            self.in_use.add(g)
-        time.sleep(self.delay)
-        with self.lock:
-            self.in_use.discard(g)
-        return g * 1000 + (req.k if req.kind == "ktruss" else 1)
+@pytest.fixture
+def fake():
+    prev = tc.tc_debug_server_fake(True)
+    yield
+    tc.tc_debug_server_fake(prev)
 
 
-def expected(req):
-    return req.graph * 1000 + (req.k if req.kind == "ktruss" else 1)
+def pool_of(sizes):
+    return {g: (np.zeros(m, np.int32), np.ones(m, np.int32), 2) for g, m in enumerate(sizes)}
 
 
-def test_all_served_once_with_overlap_and_exclusivity():
-    be = FakeBackend({g: 10 for g in range(6)})
-    srv = serve.Server(be, slots=4, budget_bytes=1000)
-    trace = serve.poisson_trace(300, rate=0, graph_ids=range(6), seed=1)
-    wall = serve.replay(srv, trace)
-    srv.shutdown()
-    reqs = [r for _, r in trace]
-    assert len(srv.completed) == 300
-    assert sorted(r.rid for r in srv.completed) == list(range(300))
-    assert all(r.result == expected(r) and r.error is None for r in reqs)
-    assert not be.violations
-    assert srv.max_concurrent >= 2
-    s = serve.summarize(reqs, wall)
-    assert s["requests"] == 300 and s["p99_ms"] >= s["p50_ms"]
+def expected(r):
+    return r.graph * 1000 + (0 if r.kind == "count" else r.k)
 
 
-def test_budget_evicts_least_recently_used():
-    sizes = {g: 40 for g in range(5)}
-    be = FakeBackend(sizes)
-    srv = serve.Server(be, slots=2, budget_bytes=100)     # two graphs fit at a time
-    trace = serve.poisson_trace(120, rate=0, graph_ids=range(5), seed=2)
-    serve.replay(srv, trace)
-    srv.shutdown()
-    assert all(r.result == expected(r) for _, r in trace)
-    assert be.peak_bytes <= 100
-    assert srv.evictions > 0 and srv.builds > 5
-
-
-def test_backend_errors_are_reported_per_request():
-    class Failing(FakeBackend):
-        def query(self, handle, req, stream):
-            if req.rid % 7 == 0:
-                raise RuntimeError("boom")
-            return super().query(handle, req, stream)
-    be = Failing({g: 1 for g in range(3)})
-    srv = serve.Server(be, slots=3, budget_bytes=100)
-    trace = serve.poisson_trace(50, rate=0, graph_ids=range(3), seed=3)
-    serve.replay(srv, trace)
-    srv.shutdown()
+def test_every_request_served_once_with_its_result(fake):
+    srv = serve.NativeServer(pool_of([1000] * 12), slots=6, budget_bytes=1 << 40)
+    trace = serve.poisson_trace(400, 0, list(range(12)), seed=3)
+    srv.run(trace, open_loop=False)
+    st = srv.stats()
     for _, r in trace:
-        if r.rid % 7 == 0:
-            assert r.error and r.result is None
-        else:
-            assert r.result == expected(r)
+        assert r.error is None and r.result == expected(r)
+        assert 0 <= r.slot < 6 and r.done >= r.start
+    assert st["violations"] == 0
+    assert st["max_concurrent"] >= 2
+    assert st["builds"] == 12 and st["evictions"] == 0
+    srv.close()
 
 
-def test_poisson_trace_shape():
-    tr = serve.poisson_trace(2000, rate=100.0, graph_ids=[1, 2, 3], seed=4)
-    times = [t for t, _ in tr]
-    assert times == sorted(times) and times[0] == 0.0
-    assert 15 < times[-1] < 25           # ~2000 / 100 s
-    kinds = [r.kind for _, r in tr]
-    assert 0.4 < kinds.count("count") / 2000 < 0.6
-    assert {r.k for _, r in tr if r.kind == "ktruss"} <= {3, 4, 5, 6, 7, 8}
+def test_budget_evicts_least_recently_used_idle_graphs(fake):
+    sizes = [200_000] * 10   # each ~29 MB reserved: 140 B per pair + 1 MiB
+    per = 140 * 200_000 + (1 << 20)
+    budget = 3 * per + 1000
+    srv = serve.NativeServer(pool_of(sizes), slots=4, budget_bytes=budget)
+    trace = serve.poisson_trace(300, 0, list(range(10)), seed=5)
+    srv.run(trace, open_loop=False)
+    st = srv.stats()
+    assert all(r.error is None and r.result == expected(r) for _, r in trace)
+    assert st["peak_reserved_bytes"] <= budget
+    assert st["evictions"] > 0 and st["builds"] == st["evictions"] + st["resident_graphs"]
+    assert st["resident_graphs"] <= 3 and st["violations"] == 0
+    srv.close()
+
+
+def test_open_loop_respects_arrivals_and_keeps_graphs_between_runs(fake):
+    srv = serve.NativeServer(pool_of([500] * 4), slots=3, budget_bytes=1 << 40)
+    trace = serve.poisson_trace(60, 2000.0, [0, 1, 2, 3], seed=9)
+    wall = srv.run(trace)
+    assert wall >= trace[-1][0]
+    for at, r in trace:
+        assert r.error is None and r.result == expected(r)
+        assert r.start >= at - 1e-6 and r.latency >= 0
+    builds = srv.stats()["builds"]
+    srv.run(serve.fresh(trace))
+    assert srv.stats()["builds"] == builds      # still resident
+    summ = serve.summarize([r for _, r in trace], wall)
+    assert summ["errors"] == 0 and summ["p99_ms"] >= summ["p50_ms"]
+    srv.close()
+
+
+def test_bad_requests_and_arguments_are_refused(fake):
+    srv = serve.NativeServer(pool_of([10, 10]), slots=2, budget_bytes=1 << 30)
+    with pytest.raises(KeyError):
+        srv.run([(0.0, serve.Request(0, 5, "count"))])
+    with pytest.raises(tc.TCError) as ei:
+        srv.run([(0.0, serve.Request(0, 1, "ktruss", 1))])
+    assert ei.value.code == tc.TC_EINVAL
+    with pytest.raises(tc.TCError):
+        srv.run([(0.5, serve.Request(0, 0, "count")), (0.1, serve.Request(1, 1, "count"))])
+    srv.close()
+    with pytest.raises(tc.TCError):
+        serve.NativeServer(pool_of([10]), slots=0)
+    with pytest.raises(tc.TCError):
+        serve.NativeServer(pool_of([10]), budget_bytes=0)
