@@ -174,16 +174,24 @@ __global__ void k_pairs(const int32_t* __restrict__ lo, const int32_t* __restric
 
 // col from the sorted keys; row boundaries -> rowptr; first entry above the
 // row -> upper (rows with none keep upper = rowptr[r + 1], set beforehand).
+// col from the sorted (row, col) keys; rowptr[r] = first entry of row r.
+// Entry i sets the offsets of the rows from its predecessor's row + 1 to its
+// own.  The rows before the first entry (the degree-0 vertices, which the
+// degree order puts first — millions of them in a large R-MAT graph) are
+// set by a separate grid-stride loop, not by entry 0's thread alone.
 __global__ void k_csr_fill(const uint64_t* __restrict__ keys, int64_t nnz, int32_t n, int bits,
                            int32_t* __restrict__ col, int64_t* __restrict__ rowptr) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const uint64_t mask = (1ull << bits) - 1;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= nnz; i += stride) {
-        const int64_t r_prev = i == 0 ? -1 : (int64_t)(keys[i - 1] >> bits);
+    const int64_t first = nnz > 0 ? (int64_t)(keys[0] >> bits) : (int64_t)n;
+    for (int64_t r = tid; r <= first; r += stride) rowptr[r] = 0;
+    for (int64_t i = tid + 1; i <= nnz; i += stride) {
+        const int64_t r_prev = (int64_t)(keys[i - 1] >> bits);
         const int64_t r_cur = i == nnz ? (int64_t)n : (int64_t)(keys[i] >> bits);
-        if (i < nnz) col[i] = (int32_t)(keys[i] & mask);
         for (int64_t r = r_prev + 1; r <= r_cur; ++r) rowptr[r] = i;
     }
+    for (int64_t i = tid; i < nnz; i += stride) col[i] = (int32_t)(keys[i] & mask);
 }
 
 __global__ void k_upper_init(const int64_t* __restrict__ rowptr, int32_t n,
