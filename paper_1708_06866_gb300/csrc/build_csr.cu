@@ -237,6 +237,24 @@ __global__ void k_row_stats(const int64_t* __restrict__ rowptr, const int64_t* _
 
 // Internal edge ids: position in the oriented (u, v) order.  fwd[j] is the
 // canonical id of internal edge j; inv is its inverse.
+__global__ void k_out_degree(const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
+                             int32_t n, int32_t* __restrict__ dout) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride)
+        dout[r] = (int32_t)(rowptr[r + 1] - upper[r]);
+}
+
+// Internal ids number the out-entries in CSR order: the first out-edge of
+// row r is edge obase[r] (the out-degrees before r), so entry p is edge
+// p - (upper[r] - obase[r]).
+__global__ void k_oshift(const int64_t* __restrict__ upper,
+                         const unsigned long long* __restrict__ obase, int32_t n,
+                         int64_t* __restrict__ oshift) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride)
+        oshift[r] = upper[r] - (int64_t)obase[r];
+}
+
 __global__ void k_invert(const int32_t* __restrict__ fwd, int64_t m, int32_t* __restrict__ inv) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
@@ -381,6 +399,18 @@ int build_graph(Graph* g, const int32_t* src, const int32_t* dst, cudaStream_t s
             TC_LAUNCH_CHECK("k_gather_ends");
             dev_free(g->ends, s);
             g->ends = ends2;
+        }
+        {
+            int32_t* dout;
+            unsigned long long* obase;
+            TC_TRY(sc.alloc(&dout, n));
+            TC_TRY(sc.alloc(&obase, (int64_t)n + 1));
+            k_out_degree<<<grid_for(n), 256, 0, s>>>(g->rowptr, g->upper, n, dout);
+            TC_LAUNCH_CHECK("k_out_degree");
+            TC_TRY(exclusive_scan_i32(dout, n, obase, sc, s));
+            TC_TRY(dev_alloc_n(&g->oshift, n, s));
+            k_oshift<<<grid_for(n), 256, 0, s>>>(g->upper, obase, n, g->oshift);
+            TC_LAUNCH_CHECK("k_oshift");
         }
         TC_CUDA_TRY(cudaMemsetAsync(g->dev_scalars, 0, 2 * sizeof(unsigned long long), s));
         k_row_stats<<<grid_for(n), 256, 0, s>>>(g->rowptr, g->upper, n, g->dev_scalars);

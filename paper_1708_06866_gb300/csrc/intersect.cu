@@ -80,7 +80,7 @@ __device__ __forceinline__ int table_find(const int32_t* keys, int log_cap, int3
 template <int MODE>
 __global__ void __launch_bounds__(RX_THREADS) k_rows(
     const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
-    const int32_t* __restrict__ col, const int32_t* __restrict__ eid, int32_t n,
+    const int32_t* __restrict__ col, const int64_t* __restrict__ oshift, int32_t n,
     int32_t* __restrict__ sup, const unsigned long long* __restrict__ off,
     unsigned int* __restrict__ top, int2* __restrict__ pairs, unsigned int* __restrict__ next_row,
     unsigned long long* __restrict__ partials, int max_log_cap, int max_pos) {
@@ -107,6 +107,8 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
         if (r >= n) break;
         const int32_t u = n - 1 - r;
         const int64_t a0 = upper[u];
+        // the out-edges of a row have consecutive ids: id of entry p = p - oshift[row]
+        const int64_t eu = a0 - (MODE == COUNT ? 0 : oshift[u]);
         const int du = (int)(rowptr[u + 1] - a0);
         if (du < 2) continue;
         // clamped to the block's table (never binding when sized as the host
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
             for (int i = threadIdx.x; i < du; i += RX_THREADS) cnt[i] = 0;
         if (MODE == LISTS)
             for (int i = threadIdx.x; i < du; i += RX_THREADS) {
-                const int32_t e = eid[a0 + i];
+                const int32_t e = (int32_t)(eu + i);
                 cnt[i] = 0;
                 seid[i] = e;
                 sbase[i] = (unsigned int)off[e];
@@ -136,7 +138,8 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
         for (int j = warp; j < du - 1; j += RX_WARPS) {
             const int32_t v = col[a0 + j];
             const int64_t b0 = upper[v], b1 = rowptr[v + 1];
-            const int32_t e_uv = MODE == COUNT ? 0 : MODE == LISTS ? seid[j] : eid[a0 + j];
+            const int64_t ov = MODE == COUNT ? 0 : oshift[v];
+            const int32_t e_uv = MODE == COUNT ? 0 : (int32_t)(eu + j);
             const unsigned int base_uv = MODE == LISTS ? sbase[j] : 0u;
             uint32_t c = 0;
             // one hit: credit the triangle (u, v, w) found at N+(v) position p,
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
                 ++c;
                 if (MODE == SUPPORT) {
                     atomicAdd(&cnt[pos[h]], 1);
-                    atomicAdd(&sup[eid[p]], 1);
+                    atomicAdd(&sup[p - ov], 1);
                 }
             };
             // the triangles of a chunk share edge (u, v): one append for all;
@@ -160,7 +163,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
                 base = __shfl_sync(0xffffffffu, base, ldr);
                 if (h >= 0) {
                     const int iw = pos[h];
-                    const int32_t e_uw = seid[iw], e_vw = eid[p];
+                    const int32_t e_uw = seid[iw], e_vw = (int32_t)(p - ov);
                     pairs[base_uv + base + __popc(msk & lanemask_lt())] = make_int2(e_uw, e_vw);
                     pairs[sbase[iw] + atomicAdd((unsigned int*)&cnt[iw], 1u)] =
                         make_int2(e_uv, e_vw);
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
         __syncthreads();
         if (MODE == SUPPORT)
             for (int i = threadIdx.x; i < du; i += RX_THREADS)
-                if (cnt[i]) atomicAdd(&sup[eid[a0 + i]], cnt[i]);
+                if (cnt[i]) atomicAdd(&sup[eu + i], cnt[i]);
         __syncthreads();
     }
     if (lane == 0) s_acc[warp] = acc;
@@ -219,7 +222,7 @@ template <int MODE>
 __global__ void __launch_bounds__(IX_THREADS) k_edges_thread(
     const int2* __restrict__ ends, const int64_t* __restrict__ rowptr,
     const int64_t* __restrict__ upper, const int32_t* __restrict__ col,
-    const int32_t* __restrict__ eid, int64_t m, int32_t* __restrict__ sup,
+    const int64_t* __restrict__ oshift, int64_t m, int32_t* __restrict__ sup,
     unsigned int* __restrict__ top, int2* __restrict__ pairs,
     unsigned long long* __restrict__ partials) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -228,6 +231,8 @@ __global__ void __launch_bounds__(IX_THREADS) k_edges_thread(
         const int2 uv = ends[j];
         int64_t a = upper[uv.x], b = upper[uv.y];
         const int64_t a1 = rowptr[uv.x + 1], b1 = rowptr[uv.y + 1];
+        const int64_t ou = MODE == COUNT ? 0 : oshift[uv.x];
+        const int64_t ov = MODE == COUNT ? 0 : oshift[uv.y];
         uint32_t c = 0;
         while (a < a1 && b < b1) {
             const int32_t x = col[a], y = col[b];
@@ -238,11 +243,12 @@ __global__ void __launch_bounds__(IX_THREADS) k_edges_thread(
             } else {
                 ++c;
                 if (MODE == SUPPORT) {
-                    atomicAdd(&sup[eid[a]], 1);
-                    atomicAdd(&sup[eid[b]], 1);
+                    atomicAdd(&sup[a - ou], 1);
+                    atomicAdd(&sup[b - ov], 1);
                 }
                 if (MODE == LISTS) {
-                    const int32_t e_uw = eid[a], e_vw = eid[b], e_uv = (int32_t)j;
+                    const int32_t e_uw = (int32_t)(a - ou), e_vw = (int32_t)(b - ov);
+                    const int32_t e_uv = (int32_t)j;
                     pairs[atomicSub(&top[e_uv], 1u) - 1u] = make_int2(e_uw, e_vw);
                     pairs[atomicSub(&top[e_uw], 1u) - 1u] = make_int2(e_uv, e_vw);
                     pairs[atomicSub(&top[e_vw], 1u) - 1u] = make_int2(e_uv, e_uw);
@@ -271,7 +277,7 @@ template <bool SUPPORT>
 __global__ void __launch_bounds__(IX_THREADS) k_edges_warp(
     const int2* __restrict__ ends,
     const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
-    const int32_t* __restrict__ col, const int32_t* __restrict__ eid, int64_t m,
+    const int32_t* __restrict__ col, const int64_t* __restrict__ oshift, int64_t m,
     int32_t* __restrict__ sup, unsigned long long* __restrict__ partials) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -282,12 +288,15 @@ __global__ void __launch_bounds__(IX_THREADS) k_edges_warp(
         const int2 uv = ends[e];
         int64_t s0 = upper[uv.x], s1 = rowptr[uv.x + 1];
         int64_t l0 = upper[uv.y], l1 = rowptr[uv.y + 1];
+        int64_t os = SUPPORT ? oshift[uv.x] : 0, ol = SUPPORT ? oshift[uv.y] : 0;
         if (s1 - s0 > l1 - l0) {
-            const int64_t t0 = s0, t1 = s1;
+            const int64_t t0 = s0, t1 = s1, t2 = os;
             s0 = l0;
             s1 = l1;
+            os = ol;
             l0 = t0;
             l1 = t1;
+            ol = t2;
         }
         if (s0 == s1) continue;
         uint32_t cnt = 0;
@@ -302,8 +311,8 @@ __global__ void __launch_bounds__(IX_THREADS) k_edges_warp(
             if (lo < l1 && col[lo] == w) {
                 ++cnt;
                 if (SUPPORT) {
-                    atomicAdd(&sup[eid[p]], 1);
-                    atomicAdd(&sup[eid[lo]], 1);
+                    atomicAdd(&sup[p - os], 1);
+                    atomicAdd(&sup[lo - ol], 1);
                 }
             }
         }
@@ -497,7 +506,7 @@ int launch_rows(Graph* g, int32_t* sup, const unsigned long long* off, unsigned 
     const size_t sm = rows_smem(lc, MODE, max_pos);
     unsigned int* next_row = reinterpret_cast<unsigned int*>(g->dev_scalars + 4);
     TC_CUDA_TRY(cudaMemsetAsync(next_row, 0, sizeof(unsigned int), s));
-    k_rows<MODE><<<blocks, RX_THREADS, sm, s>>>(g->rowptr, g->upper, g->col, g->eid, g->n, sup,
+    k_rows<MODE><<<blocks, RX_THREADS, sm, s>>>(g->rowptr, g->upper, g->col, g->oshift, g->n, sup,
                                                 off, top, pairs, next_row, partials, lc,
                                                 max_pos);
     TC_LAUNCH_CHECK("k_rows");
@@ -577,19 +586,19 @@ int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangle
     } else if (f == 3) {
         if (want_support)
             k_edges_thread<SUPPORT><<<blocks, IX_THREADS, 0, s>>>(
-                g->ends, g->rowptr, g->upper, g->col, g->eid, m, sup, nullptr, nullptr, partials);
+                g->ends, g->rowptr, g->upper, g->col, g->oshift, m, sup, nullptr, nullptr, partials);
         else
             k_edges_thread<COUNT><<<blocks, IX_THREADS, 0, s>>>(
-                g->ends, g->rowptr, g->upper, g->col, g->eid, m, nullptr, nullptr, nullptr,
+                g->ends, g->rowptr, g->upper, g->col, g->oshift, m, nullptr, nullptr, nullptr,
                 partials);
         TC_LAUNCH_CHECK("k_edges_thread");
     } else if (want_support) {
         k_edges_warp<true><<<blocks, IX_THREADS, 0, s>>>(g->ends, g->rowptr, g->upper,
-                                                         g->col, g->eid, m, sup, partials);
+                                                         g->col, g->oshift, m, sup, partials);
         TC_LAUNCH_CHECK("k_edges_warp");
     } else {
         k_edges_warp<false><<<blocks, IX_THREADS, 0, s>>>(g->ends, g->rowptr, g->upper,
-                                                          g->col, g->eid, m, nullptr, partials);
+                                                          g->col, g->oshift, m, nullptr, partials);
         TC_LAUNCH_CHECK("k_edges_warp");
     }
     TC_TRY(timer.stop(s));
@@ -625,6 +634,24 @@ int to_canonical_i32(const int32_t* in, const int32_t* fwd, int64_t m, int32_t* 
     return TC_OK;
 }
 
+int exclusive_scan_i32(const int32_t* x, int64_t n, unsigned long long* out, Scratch& sc,
+                       cudaStream_t s) {
+    if (n <= 0) {
+        TC_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(unsigned long long), s));
+        return TC_OK;
+    }
+    const int64_t chunks = (n + SC_CHUNK - 1) / SC_CHUNK;
+    unsigned long long* sums;
+    TC_TRY(sc.alloc(&sums, chunks));
+    k_chunk_sums<<<(unsigned)chunks, SC_THREADS, 0, s>>>(x, n, sums);
+    TC_LAUNCH_CHECK("k_chunk_sums");
+    k_scan_sums64<<<1, 1024, 0, s>>>(sums, chunks);
+    TC_LAUNCH_CHECK("k_scan_sums64");
+    k_chunk_scan<<<(unsigned)chunks, SC_THREADS, 0, s>>>(x, n, sums, out);
+    TC_LAUNCH_CHECK("k_chunk_scan");
+    return TC_OK;
+}
+
 int plan_triangle_lists(Graph* g, Scratch& sc, ListsPlan* lp) {
     const int64_t m = g->m;
     lp->chunks = (m + SC_CHUNK - 1) / SC_CHUNK;
@@ -655,7 +682,7 @@ int enqueue_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off
     TC_TRY(lp->timer.start(s));
     if (lp->thread) {
         k_edges_thread<LISTS><<<lp->blocks, IX_THREADS, 0, s>>>(
-            g->ends, g->rowptr, g->upper, g->col, g->eid, m, nullptr, lp->top, pairs,
+            g->ends, g->rowptr, g->upper, g->col, g->oshift, m, nullptr, lp->top, pairs,
             lp->partials);
         TC_LAUNCH_CHECK("k_edges_thread");
     } else {

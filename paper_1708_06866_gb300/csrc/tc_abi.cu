@@ -110,6 +110,7 @@ void free_graph(Graph* g) {
     dev_free(g->col, s);
     dev_free(g->eid, s);
     dev_free(g->fwd, s);
+    dev_free(g->oshift, s);
     dev_free(g->support, s);
     dev_free(g->tri_off, s);
     dev_free(g->tri_pairs, s);
@@ -353,7 +354,7 @@ int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream) {
     info->max_out = gg->max_out;
     info->wedge_work = ww;
     const int64_t m = gg->m, n = gg->n;
-    info->device_bytes = m * (4 + 4 + 8 + 4 + 4 + 4) + 8 * (n + 1) + 8 * n +
+    info->device_bytes = m * (4 + 4 + 8 + 4 + 4 + 4) + 8 * (n + 1) + 8 * n + 8 * n +
                          (gg->support ? 4 * m : 0) +
                          (gg->tri_valid ? 8 * (m + 1) + 24 * gg->triangles : 0) +
                          (gg->kt_state ? 8 * m : 0) + (gg->truss_cache ? 4 * m : 0) + (gg->kt_col ? 16 * m + 4 * n : 0);

@@ -228,6 +228,9 @@ struct Graph {
     int32_t* col = nullptr;   // 2m neighbour rank ids
     int32_t* eid = nullptr;   // 2m internal edge ids
     int32_t* fwd = nullptr;   // canonical id of each internal edge
+    // internal ids follow the out-lists: the out-entry at position p of row r
+    // is edge p - oshift[r] (n entries)
+    int64_t* oshift = nullptr;
     int32_t max_out = 0;      // max |N+(u)|
     int32_t max_deg = 0;
     int64_t wedge_work = -1;  // sum of |N+(u)| + |N+(v)| over oriented edges (lazy)
@@ -283,6 +286,9 @@ struct ListsPlan {
     KernelTimer timer;
 };
 int plan_triangle_lists(Graph* g, Scratch& sc, ListsPlan* lp);
+// out[i] = x[0] + ... + x[i-1] for i in [0, n] (n + 1 entries).
+int exclusive_scan_i32(const int32_t* x, int64_t n, unsigned long long* out, Scratch& sc,
+                       cudaStream_t s);
 int enqueue_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off, int2* pairs,
                            ListsPlan* lp, cudaStream_t s);
 
