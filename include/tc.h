@@ -204,13 +204,17 @@ int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream);
 int tc_graph_wedge_work(tc_graph* g, int64_t* out, void* cuda_stream);
 
 /*
- * Bounds the optional device memory the library may use for this graph
- * beyond its CSR, edge arrays and call scratch: the per-edge triangle lists
- * of the peel (24 bytes per triangle, used only when they fit), their cache,
- * and the cached compacted adjacency of the latest ktruss.  bytes < 0 (the
- * default): a share of the device's free memory at each call.  Results do
- * not depend on it; memory use and speed do.  A serving loop sets it to keep
- * many resident graphs within a device-memory budget.
+ * Bounds the optional device memory the library may keep for this graph
+ * beyond its CSR, edge arrays, supports and call scratch: the per-edge
+ * triangle lists of the peel (24 bytes per triangle + 8 per edge), the
+ * compacted adjacency of the latest ktruss (16 bytes per edge + 4 per
+ * vertex) and the truss numbers of the latest ktruss_max (4 bytes per
+ * edge), all of them together.  The triangle-list form of the peel is used
+ * only when its lists fit.  bytes < 0 (the default): each structure may take
+ * a share of the device's free memory at the call.  Results do not depend on
+ * it; memory use and speed do.  A serving loop sets it to keep many resident
+ * graphs within a device-memory budget.  Takes effect at the next call;
+ * structures above a lowered bound are released then.
  */
 int tc_graph_set_memory_limit(tc_graph* g, int64_t bytes);
 

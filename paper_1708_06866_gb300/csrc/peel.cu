@@ -650,6 +650,27 @@ struct PeelPlan {
 };
 
 PeelPlan* peel_plan_new() { return new (std::nothrow) PeelPlan(); }
+
+namespace {
+// Optional memory the graph keeps now: triangle lists, the compacted
+// adjacency of the latest k-truss, truss numbers.
+double lists_bytes(const Graph* g) {
+    return 24.0 * (double)std::max<int64_t>(g->triangles, 0) + 8.0 * (double)(g->m + 1);
+}
+double adj_bytes(const Graph* g) { return 16.0 * (double)g->m + 4.0 * (double)g->n; }
+double kept_optional_bytes(const Graph* g) {
+    return (g->tri_off ? lists_bytes(g) : 0.0) + (g->kt_col ? adj_bytes(g) : 0.0) +
+           (g->truss_cache ? 4.0 * (double)g->m : 0.0);
+}
+// Whether a structure of `bytes` (counted in `kept_optional_bytes` when
+// `held`) may be kept: with a bound, everything kept stays within it; without
+// one, the structure fits a share of the free device memory.
+bool may_keep(const Graph* g, double bytes, bool held, double free_share) {
+    if (g->mem_limit >= 0)
+        return kept_optional_bytes(g) - (held ? bytes : 0.0) + bytes <= (double)g->mem_limit;
+    return held || bytes <= free_share;
+}
+}  // namespace
 void peel_plan_delete(PeelPlan* p) { delete p; }
 
 int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single, int32_t* t,
@@ -683,15 +704,12 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
     // list positions are 32-bit: the triangle-list form needs 3T < 2^32
     size_t free_b = 0, total_b = 0;
     TC_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    // optional memory (lists, caches) stays within the graph's limit, or a
-    // share of the free memory when the caller set none
-    const double allowance =
-        g->mem_limit >= 0 ? (double)g->mem_limit : 0.6 * (double)free_b;
+    // optional memory (lists, caches) stays within the graph's bound, all of
+    // it together, or a share of the free memory when the caller set none
     if (triangle_lists_supported(g) && forced != PEEL_INTERSECT &&
         3 * g->triangles < 0xffffffffLL) {
-        const double need = 24.0 * (double)g->triangles + 16.0 * (double)(m + 1);
-        p.tl = forced == PEEL_LISTS || need <= allowance ||
-               (g->tri_valid && g->mem_limit < 0);
+        p.tl = forced == PEEL_LISTS ||
+               may_keep(g, lists_bytes(g), g->tri_off != nullptr, 0.6 * (double)free_b);
     }
     if (!p.tl && g->tri_off) {  // cached lists above a lowered limit are dropped
         dev_free(g->tri_off, g->last_stream);
@@ -726,8 +744,8 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
     } else if (p.cache) {
         // the compacted adjacency stays with the graph when it fits
         p.fresh_adj = !(p.resume && g->kt_adj);
-        const double adj_bytes = (double)(16 * m + 4 * (int64_t)g->n);
-        if (g->kt_col && g->mem_limit >= 0 && adj_bytes > (double)g->mem_limit) {
+        const bool adj_ok = may_keep(g, adj_bytes(g), g->kt_col != nullptr, 0.4 * (double)free_b);
+        if (g->kt_col && !adj_ok) {
             dev_free(g->kt_col, g->last_stream);  // above a lowered limit
             dev_free(g->kt_eid, g->last_stream);
             dev_free(g->kt_rowlen, g->last_stream);
@@ -736,9 +754,7 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
             g->kt_adj = false;
             p.fresh_adj = true;
         }
-        const bool room = g->kt_col || (g->mem_limit >= 0 ? adj_bytes <= (double)g->mem_limit
-                                                          : adj_bytes < 0.4 * (double)free_b);
-        if (room) {
+        if (adj_ok) {
             if (!g->kt_col) {
                 TC_TRY(dev_alloc_n(&g->kt_col, 2 * m, g->last_stream));
                 TC_TRY(dev_alloc_n(&g->kt_eid, 2 * m, g->last_stream));
@@ -960,14 +976,15 @@ int peel_decompose(Graph* g, int32_t* truss, int32_t* kmax, cudaStream_t s) {
     TC_TRY(run_peel(g, 3, false, nullptr, truss, &r, s));
     *kmax = r.kmax;
     // keep the decomposition when it fits the graph's optional memory
-    const double bytes = 4.0 * (double)m;
-    bool room = g->truss_cache != nullptr;
-    if (!room) {
-        size_t free_b = 0, total_b = 0;
-        TC_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-        room = g->mem_limit >= 0 ? bytes <= (double)g->mem_limit : bytes < 0.4 * (double)free_b;
-        if (room) TC_TRY(dev_alloc_n(&g->truss_cache, m, s));
+    size_t free_b = 0, total_b = 0;
+    TC_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    bool room = may_keep(g, 4.0 * (double)m, g->truss_cache != nullptr, 0.4 * (double)free_b);
+    if (!room && g->truss_cache) {
+        dev_free(g->truss_cache, s);
+        g->truss_cache = nullptr;
+        g->truss_valid = false;
     }
+    if (room && !g->truss_cache) TC_TRY(dev_alloc_n(&g->truss_cache, m, s));
     if (room) {
         TC_CUDA_TRY(cudaMemcpyAsync(g->truss_cache, truss, sizeof(int32_t) * m,
                                     cudaMemcpyDeviceToDevice, s));

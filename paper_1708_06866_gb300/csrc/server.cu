@@ -41,7 +41,8 @@ struct Entry {
     bool resident = false;
     bool busy = false;
     bool building = false;
-    bool indexed = false;
+    bool indexed = false;     // its truss decomposition is kept
+    bool index_tried = false;  // ... or could not be (memory bound): peel per request
     int64_t reserved = 0;
     uint64_t last_use = 0;
     std::atomic<int> in_call{0};  // fake mode: concurrent calls seen on the graph
@@ -93,7 +94,8 @@ int execute(tc_server* s, Slot& slot, int32_t gid, const tc_request& rq, int64_t
     }
     if (rq.kind == TC_REQ_COUNT) return tc_count(e.g, result, slot.stream);
     if (rq.kind != TC_REQ_KTRUSS) return tc::fail(TC_EINVAL, "server: unknown request kind");
-    if (!e.indexed) {
+    if (!e.indexed && !e.index_tried) {
+        e.index_tried = true;
         int32_t kmax = 0;
         TC_TRY(ktruss_max(e.g, &kmax, nullptr, slot.stream));
         tc_graph_info_t info;
@@ -198,6 +200,7 @@ void worker(tc_server* s, int slot_id, const tc_request* reqs, int64_t nreq, boo
                     v.g = nullptr;
                     v.resident = false;
                     v.indexed = false;
+                    v.index_tried = false;
                     s->reserved -= v.reserved;
                     v.reserved = 0;
                     ++s->stats.evictions;
