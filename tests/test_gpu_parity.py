@@ -568,3 +568,31 @@ def test_kept_decomposition_answers_ktruss():
     assert tc.tc_graph_info(g2)["truss_cached"] == 0
     tc.tc_graph_free(g2)
     tc.tc_graph_free(g)
+
+
+def test_memory_bound_counts_everything_kept_together():
+    """With a bound that holds the triangle lists but not the lists and the
+    truss numbers together, ktruss_max keeps the lists and not the truss
+    numbers; results are unchanged and what the graph keeps stays within
+    the bound."""
+    src, dst, n = graphgen.rmat(11, seed=23)
+    og = oracle.OracleGraph.from_edges(src, dst, n)
+    want_kmax, want_truss = og.truss_decomposition()
+    g = tc.tc_build_csr(dev(src), dev(dst), n)
+    T = tc.tc_count(g)
+    m = g.m
+    lists = 24 * T + 8 * (m + 1)
+    tc.tc_graph_set_memory_limit(g, lists + 2 * m)      # room for lists, not 4 B per edge more
+    base = tc.tc_graph_info(g)["device_bytes"]
+    kmax, truss = tc.ktruss_max(g)
+    info = tc.tc_graph_info(g)
+    assert kmax == want_kmax and np.array_equal(truss.cpu().numpy(), want_truss)
+    assert info["peel_lists"] == 1 and info["truss_cached"] == 0
+    # lowering the bound releases the lists at the next call
+    tc.tc_graph_set_memory_limit(g, 4 * m)
+    kmax, truss = tc.ktruss_max(g)
+    info2 = tc.tc_graph_info(g)
+    assert kmax == want_kmax and np.array_equal(truss.cpu().numpy(), want_truss)
+    assert info2["peel_lists"] == 0 and info2["truss_cached"] == 1
+    assert info2["device_bytes"] < info["device_bytes"]
+    tc.tc_graph_free(g)
