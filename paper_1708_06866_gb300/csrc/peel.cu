@@ -59,6 +59,7 @@ struct PeelCtl {
     unsigned long long cntW[2];  // window-list appends, by level parity
     unsigned long long cntF[2];  // light-frontier appends, by round parity
     unsigned long long cntH[2];  // heavy-frontier appends, by round parity
+    int minenc[3];               // per level (mod 3): INT_MAX - smallest alive support scanned
     int abort;                   // 1 = a barrier wait ran out of time
     int kmax;                    // decomposition result
     int overflow;                // 1 = the round table ran out (not expected)
@@ -445,6 +446,10 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
             const int32_t* in = full ? (first ? nullptr : a.A[ai]) : a.W[wi];
             const int64_t n_in = full ? nA : nW;
             int32_t* Aout = a.A[ai ^ 1];
+            const int ms = level % 3;
+            // the slot the level after next uses: clear it for that level
+            if (leader) ctl->minenc[(level + 1) % 3] = 0;
+            int smin = INT_MAX;  // smallest support among the alive edges scanned
             for (int64_t base = gwarp * 32; base < n_in; base += nwarps * 32) {
                 const int64_t i = base + lane;
                 bool alive = false, win = false, light = false, heavy = false;
@@ -455,6 +460,7 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
                     alive = ld_cg(a.t + e) == 0;
                     if (alive) {
                         const int32_t se = ld_cg(a.s + e);
+                        smin = min(smin, se);
                         win = se < bound;
                         if (se < thr) {
                             a.t[e] = -r;
@@ -468,6 +474,8 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
                 warp_append(light, e, a.F[fi], &ctl->cntF[pf], baseF[pf]);
                 warp_append(heavy, e, a.H[fi], &ctl->cntH[pf], baseH[pf]);
             }
+            smin = __reduce_min_sync(0xffffffffu, smin);
+            if (lane == 0 && smin != INT_MAX) atomicMax(&ctl->minenc[ms], INT_MAX - smin);
         }
         if (!grid_sync(ctl, &epoch, a.spin_ns, &s_ok)) return;
         if (full) {
@@ -486,6 +494,15 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
             nH = (int64_t)(eH - baseH[pf]);
             baseF[pf] = eF;
             baseH[pf] = eH;
+        }
+        // no edge below the threshold: levels up to the smallest alive
+        // support + 2 remove nothing either (their k-trusses are all alive
+        // edges), so the next level to peel is that support + 3
+        int32_t k_next = k + 1;
+        if (nF + nH == 0) {
+            int32_t m0 = INT_MAX - *(volatile int*)&ctl->minenc[level % 3];
+            if (!full) m0 = min(m0, bound);  // edges outside the window have s >= bound
+            if (m0 != INT_MAX && m0 + 3 > k_next) k_next = m0 + 3;
         }
         ++level;
 
@@ -554,8 +571,8 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
         ++r;
         if (a.single) break;
         if (n_alive == 0) break;
-        kmax = k;
-        ++k;
+        kmax = k_next - 1;
+        k = k_next;
     }
     atomicAdd(&ctl->scanned, tl.scanned);
     atomicAdd(&ctl->entries, tl.entries);
