@@ -36,10 +36,13 @@ namespace {
 #endif
 constexpr int PK_THREADS = TC_PK_THREADS;
 constexpr int PK_WARPS = PK_THREADS / 32;
-constexpr int WINDOW = 8;        // support values one full scan covers (see k_peel)
+#ifndef TC_PK_WINDOW
+#define TC_PK_WINDOW 16
+#endif
+constexpr int WINDOW = TC_PK_WINDOW;  // support values one full scan covers (see k_peel)
 constexpr int64_t HEAVY = 4096;  // triangle-list length above which an edge is "heavy"
 #ifndef TC_PK_LANE_EDGES
-#define TC_PK_LANE_EDGES 8           // frontier edges per warp from which lanes take one each
+#define TC_PK_LANE_EDGES 32          // frontier edges per warp from which lanes take one each
 #endif
 #ifndef TC_PK_SHORT_LIST
 #define TC_PK_SHORT_LIST 32          // ... and walk lists up to this length alone
