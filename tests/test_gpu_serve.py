@@ -67,3 +67,30 @@ def test_budget_forces_eviction_and_rebuild_on_gpu():
     alone = alone_results(pool)
     for _, r in trace:
         assert r.error is None and r.result == alone[(r.graph, r.kind, r.k)], r
+
+
+def test_failed_allocation_fails_one_request_and_the_server_goes_on():
+    """An injected device-allocation failure during a run (on the host: the
+    library's allocation hook) fails the request that hit it with TC_ENOMEM;
+    every other request in the run still gets its exact result, and the next
+    run on the same server succeeds throughout."""
+    pool = graphgen.rmat_pool(6, seed=21, n_min=1 << 8, n_max=1 << 11)
+    alone = alone_results(pool)
+    srv = serve.NativeServer(pool, slots=3, budget_bytes=4 << 30)
+    trace = serve.poisson_trace(60, rate=0, graph_ids=list(pool), seed=22)
+    tc.tc_debug_fail_alloc(25)          # the 25th device allocation from now fails
+    try:
+        srv.run(trace, open_loop=False)
+    finally:
+        tc.tc_debug_fail_alloc(0)
+    failed = [r for _, r in trace if r.error is not None]
+    assert 1 <= len(failed) <= 2, [r.error for r in failed]
+    assert all("code -3" in r.error for r in failed)
+    for _, r in trace:
+        if r.error is None:
+            assert r.result == alone[(r.graph, r.kind, r.k)], r
+    again = serve.fresh(trace)
+    srv.run(again, open_loop=False)
+    assert all(r.error is None and r.result == alone[(r.graph, r.kind, r.k)] for _, r in again)
+    assert srv.stats()["errors"] == len(failed)
+    srv.close()
