@@ -8,9 +8,6 @@
 
 #include "tc_internal.cuh"
 
-struct tc_graph {
-    tc::Graph g;
-};
 
 namespace tc {
 

@@ -331,3 +331,8 @@ int truss_components(Graph* g, int32_t k, int32_t* edge_label, int32_t* vertex_l
                      int64_t* count, cudaStream_t s);
 
 }  // namespace tc
+
+// The ABI's opaque graph handle.
+struct tc_graph {
+    tc::Graph g;
+};
