@@ -94,3 +94,28 @@ def test_failed_allocation_fails_one_request_and_the_server_goes_on():
     assert all(r.error is None and r.result == alone[(r.graph, r.kind, r.k)] for _, r in again)
     assert srv.stats()["errors"] == len(failed)
     srv.close()
+
+
+def test_server_degenerate_graphs_and_k2():
+    """Graphs with no edges, a single vertex, only loops and repeats, and a
+    clique, served together; k = 2 (every edge) and k above kmax."""
+    empty = (np.zeros(0, np.int32), np.zeros(0, np.int32), 5)
+    single = (np.zeros(0, np.int32), np.zeros(0, np.int32), 1)
+    loops = (np.array([0, 1, 1, 2], np.int32), np.array([0, 1, 1, 2], np.int32), 3)
+    clique = graphgen.complete(7)
+    pool = {0: empty, 1: single, 2: loops, 3: clique}
+    want = {(0, "count", 0): 0, (1, "count", 0): 0, (2, "count", 0): 0, (3, "count", 0): 35}
+    for g in (0, 1, 2):
+        for k in (2, 3, 9):
+            want[(g, "ktruss", k)] = 0
+    for k in (2, 3, 7, 8, 9):
+        want[(3, "ktruss", k)] = 21 if k <= 7 else 0
+    trace = []
+    for i, (key, _) in enumerate(sorted(want.items()) * 3):
+        g, kind, k = key
+        trace.append((0.0, serve.Request(i, g, kind, k)))
+    srv = serve.NativeServer(pool, slots=4, budget_bytes=1 << 30)
+    srv.run(trace, open_loop=False)
+    srv.close()
+    for _, r in trace:
+        assert r.error is None and r.result == want[(r.graph, r.kind, r.k)], r
