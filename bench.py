@@ -471,6 +471,9 @@ def bench_ours(args, rank, world):
                       "l2": f"flushed between steps ({args.flush_mb} MB write)",
                       "parallelism": "replicas" if world > 1 else "single"},
            "phases_ms": {k: round(float(np.mean(v)), 3) for k, v in phases.items()},
+           "phases_note": "support: one masked-product pass gives the supports and T "
+                          "(T = sum(s)/3); count: tc_count returns that T (no launch); "
+                          "truss: triangle-list build (when the lists fit) + peel",
            "roofline": roofline, "kernels": kernels, "peel_work_per_launch": peel_work,
            "gpu_launches": launches,
            "clocks": sampler.summary(),
