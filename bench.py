@@ -302,7 +302,8 @@ def bench_batch(args, rank, world):
                        "build_ms": float(np.mean([s_["build_ns"] for s_ in stats])) / 1e6,
                        "query_ms": float(np.mean([s_["query_ns"] for s_ in stats])) / 1e6,
                        "tuner": {k_: stats[-1][k_] for k_ in ("intersect_form", "peel_form",
-                                                              "tuned_from_cache", "captured")},
+                                                              "peel_blocks", "tuned_from_cache",
+                                                              "captured")},
                        "l2": f"flushed between steps ({args.flush_mb} MB write)",
                        "parallelism": "single"},
             "gpu_launches": launches, "clocks": sampler.summary()}

@@ -370,6 +370,8 @@ typedef struct {
     int32_t peel_form;         /* 0 = no peel, 1 = triangle lists, 2 = intersections */
     int32_t tuned_from_cache;  /* 1 if the kernel choice came from the tuner's cache */
     int32_t captured;          /* 1 if the query ran as one CUDA graph launch */
+    int32_t peel_blocks;       /* the tuner's cap on the peel's grid (0 = none) */
+    int32_t pad;
 } tc_batch_stats_t;
 
 typedef struct {

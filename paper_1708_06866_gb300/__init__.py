@@ -148,7 +148,8 @@ class BatchStats(ctypes.Structure):
     _fields_ = [("build_ns", ctypes.c_int64), ("query_ns", ctypes.c_int64),
                 ("m", ctypes.c_int64), ("triangles", ctypes.c_int64),
                 ("intersect_form", ctypes.c_int32), ("peel_form", ctypes.c_int32),
-                ("tuned_from_cache", ctypes.c_int32), ("captured", ctypes.c_int32)]
+                ("tuned_from_cache", ctypes.c_int32), ("captured", ctypes.c_int32),
+                ("peel_blocks", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

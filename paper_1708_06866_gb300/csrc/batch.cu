@@ -90,8 +90,9 @@ __global__ void k_segment_sums(const T* __restrict__ x, const int64_t* __restric
 }
 
 struct Choice {
-    int intersect = 1;  // 1 row/hash kernel, 2 edge-per-warp
+    int intersect = 1;    // 1 row/hash kernel, 2 edge-per-warp, 3 edge-per-thread
     int peel = PEEL_AUTO;
+    int peel_blocks = 0;  // cap on the peel's grid (0 = its own rule)
 };
 std::mutex g_tune_mu;
 std::map<uint64_t, Choice> g_tune;
@@ -131,14 +132,19 @@ int autotune(Graph* g, int32_t k, Choice* c, cudaStream_t s) {
     Scratch sc(s);
     int32_t* t;
     TC_TRY(sc.alloc(&t, g->m));
-    for (int form : {PEEL_LISTS, PEEL_INTERSECT}) {
+    // peel form and grid: the full grid, half and a quarter of the SMs
+    // (the peel is latency-bound, so a smaller grid with cheaper barriers can win)
+    const int grids[3] = {0, std::max(1, num_sms() / 2), std::max(1, num_sms() / 4)};
+    for (int trial = 0; trial < 6; ++trial) {
+        const int form = trial < 3 ? PEEL_LISTS : PEEL_INTERSECT;
+        const int cap = grids[trial % 3];
         PeelPlan* p = peel_plan_new();
         if (!p) return fail(TC_ENOMEM, "peel plan");
         int64_t left = 0;
         int rc;
         {
             Scratch psc(s);
-            rc = peel_plan(p, psc, g, k, true, t, form);
+            rc = peel_plan(p, psc, g, k, true, t, form, false, false, cap);
             const bool skip = rc == TC_OK && form == PEEL_LISTS && !peel_uses_lists(p);
             if (rc == TC_OK && !skip) {
                 rc = peel_enqueue(p, s);
@@ -152,6 +158,7 @@ int autotune(Graph* g, int32_t k, Choice* c, cudaStream_t s) {
                     if (best_ns < 0 || ns < best_ns) {
                         best_ns = ns;
                         c->peel = form;
+                        c->peel_blocks = cap;
                     }
                 }
             }
@@ -309,7 +316,8 @@ int batch_run(const tc_batch_desc* d, cudaStream_t user_stream) {
         plan = peel_plan_new();
         if (!plan) return fail(TC_ENOMEM, "peel plan");
         pguard.p = plan;
-        TC_TRY(peel_plan(plan, sc, &g, d->k, true, t, choice.peel));
+        TC_TRY(peel_plan(plan, sc, &g, d->k, true, t, choice.peel, false, false,
+                         choice.peel_blocks));
     }
     KernelTimer query_timer;
     auto enqueue_query = [&]() -> int {
@@ -387,6 +395,7 @@ int batch_run(const tc_batch_desc* d, cudaStream_t user_stream) {
         st->triangles = tri_total;
         st->intersect_form = choice.intersect;
         st->peel_form = peel ? (peel_uses_lists(plan) ? 1 : 2) : 0;
+        st->peel_blocks = peel ? choice.peel_blocks : 0;
         st->tuned_from_cache = cached ? 1 : 0;
         st->captured = d->use_graph ? 1 : 0;
     }

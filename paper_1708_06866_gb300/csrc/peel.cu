@@ -694,7 +694,7 @@ bool may_keep(const Graph* g, double bytes, bool held, double free_share) {
 void peel_plan_delete(PeelPlan* p) { delete p; }
 
 int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single, int32_t* t,
-              int form, bool keep_lists, bool use_cache) {
+              int form, bool keep_lists, bool use_cache, int max_blocks) {
     PeelPlan& p = *pp;
     const int64_t m = g->m;
     if (!g->support_valid) return fail(TC_EINVAL, "internal: peel planned without supports");
@@ -819,6 +819,7 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
     const int64_t want = std::min<int64_t>(std::max<int64_t>(1, (m + 24575) / 24576),
                                            TC_PK_MAX_BLOCKS);
     p.blocks = (int)std::min<int64_t>(want, (int64_t)num_sms() * std::min(per_sm, 1024 / PK_THREADS));
+    if (max_blocks > 0) p.blocks = std::min(p.blocks, max_blocks);
     g->last_peel_lists = p.tl;
     return TC_OK;
 }

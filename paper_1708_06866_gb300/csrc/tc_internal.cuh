@@ -300,8 +300,9 @@ void peel_plan_delete(PeelPlan* p);
 // keep_lists: a triangle-list build is kept with the graph for later peels;
 // use_cache (single level only): work in the graph's k-truss cache and
 // resume from it when k is at least the cached k.
+// max_blocks > 0 caps the peel's grid (the batch tuner tries several).
 int peel_plan(PeelPlan* p, Scratch& sc, Graph* g, int32_t k_first, bool single, int32_t* t,
-              int form, bool keep_lists = false, bool use_cache = false);
+              int form, bool keep_lists = false, bool use_cache = false, int max_blocks = 0);
 int peel_enqueue(PeelPlan* p, cudaStream_t s);
 int peel_finish(PeelPlan* p, cudaStream_t s, int64_t* n_alive, int32_t* kmax);
 bool peel_uses_lists(const PeelPlan* p);
