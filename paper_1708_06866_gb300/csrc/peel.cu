@@ -40,7 +40,11 @@ constexpr int PK_WARPS = PK_THREADS / 32;
 #define TC_PK_WINDOW 16
 #endif
 constexpr int WINDOW = TC_PK_WINDOW;  // support values one full scan covers (see k_peel)
-constexpr int64_t HEAVY = 4096;  // triangle-list length above which an edge is "heavy"
+#ifndef TC_PK_HEAVY
+#define TC_PK_HEAVY 4096             // triangle-list length above which an edge is "heavy"
+#endif
+constexpr int64_t HEAVY = TC_PK_HEAVY;
+
 #ifndef TC_PK_LANE_EDGES
 #define TC_PK_LANE_EDGES 32          // frontier edges per warp from which lanes take one each
 #endif
@@ -53,7 +57,7 @@ constexpr int64_t SHORT_LIST = TC_PK_SHORT_LIST;
 #define TC_PK_MAX_BLOCKS (1 << 20)   // cap on the peel's grid
 #endif
 #ifndef TC_PK_UNROLL
-#define TC_PK_UNROLL 2               // triangle-list entries per lane in flight
+#define TC_PK_UNROLL 3               // triangle-list entries per lane in flight
 #endif
 
 struct PeelCtl {
@@ -97,6 +101,8 @@ struct PeelArgs {
     int32_t* W[2];    // window lists
     int32_t* F[2];    // light frontiers
     int32_t* H[2];    // heavy frontiers
+    uint2* FR[2];     // list form: triangle-list range {q0, q1} of each F entry
+    uint2* HR[2];     // ... and of each H entry
     int32_t* level_of;  // level k of each round number
     int64_t max_round;  // entries of level_of
     PeelCtl* ctl;
@@ -149,7 +155,8 @@ __device__ bool grid_sync(PeelCtl* ctl, unsigned long long* epoch, int64_t spin_
 
 __device__ __forceinline__ void warp_append(bool take, int32_t value, int32_t* list,
                                             unsigned long long* counter,
-                                            unsigned long long base) {
+                                            unsigned long long base, uint2* ranges = nullptr,
+                                            uint2 range = uint2{}) {
     const unsigned mask = __ballot_sync(0xffffffffu, take);
     if (mask == 0) return;
     const int lane = threadIdx.x & 31;
@@ -157,7 +164,11 @@ __device__ __forceinline__ void warp_append(bool take, int32_t value, int32_t* l
     unsigned long long pos = 0;
     if (lane == leader) pos = atomicAdd(counter, (unsigned long long)__popc(mask));
     pos = __shfl_sync(0xffffffffu, pos, leader);
-    if (take) list[pos - base + __popc(mask & lanemask_lt())] = value;
+    if (take) {
+        const unsigned long long q = pos - base + __popc(mask & lanemask_lt());
+        list[q] = value;
+        if (ranges) ranges[q] = range;
+    }
 }
 
 // Edge states during round r: 0 = alive; -r = in round r's frontier (dying);
@@ -175,6 +186,8 @@ struct Round {
 struct Sinks {
     int32_t* Fn;
     int32_t* Hn;
+    uint2* FRn;  // list form: the entries' list ranges
+    uint2* HRn;
     int32_t* Wc;
     unsigned long long* cntF;
     unsigned long long* cntH;
@@ -184,25 +197,52 @@ struct Sinks {
     int32_t bound;  // window bound: the window list holds alive edges with s < bound
 };
 
-template <bool TL>
-__device__ __forceinline__ bool is_heavy(const PeelArgs& a, int32_t e) {
-    return TL && (int64_t)(a.off[e + 1] - a.off[e]) > HEAVY;
+// List form: edge e's triangle list is pairs[q0, q1).  Positions are below
+// 2^32 (the list form needs 3T < 2^32).  Frontier entries carry this range,
+// so processing an entry does not wait for an offset load.
+__device__ __forceinline__ uint2 list_range(const PeelArgs& a, int32_t e) {
+    return make_uint2((unsigned)a.off[e], (unsigned)a.off[e + 1]);
 }
 
-// Lowers the support of alive edge x by one; x joins the next frontier when
-// its support falls from k - 2 to k - 3 and the window list when it falls to
-// just below the window bound (exactly one atomic sees each crossing).
+__device__ __forceinline__ bool is_heavy(uint2 rg) { return (int64_t)(rg.y - rg.x) > HEAVY; }
+
+// The crossing checks after a decrement of alive edge x returned old: x
+// joins the next frontier when its support falls from k - 2 to k - 3 and the
+// window list when it falls to just below the window bound (exactly one
+// decrement sees each crossing).  x < 0: no decrement.  The list length
+// (heavy or not) is read only for a crossing edge: reading it for every
+// decrement costs more than the extra latency of the few crossings.
+// One atomic per append: warp-aggregating these appends measured slower.
+template <bool TL>
+__device__ __forceinline__ void after_lower(const PeelArgs& a, Round rd, int32_t x, int old,
+                                            const Sinks& k) {
+    if (x < 0) return;
+    if (old == k.thr) {
+        a.t[x] = -(rd.r + 1);
+        if (TL) {
+            const uint2 rg = list_range(a, x);
+            if (is_heavy(rg)) {
+                const unsigned long long q = atomicAdd(k.cntH, 1ull) - k.baseH;
+                k.Hn[q] = x;
+                k.HRn[q] = rg;
+            } else {
+                const unsigned long long q = atomicAdd(k.cntF, 1ull) - k.baseF;
+                k.Fn[q] = x;
+                k.FRn[q] = rg;
+            }
+        } else {
+            k.Fn[atomicAdd(k.cntF, 1ull) - k.baseF] = x;
+        }
+    }
+    if (old == k.bound) k.Wc[atomicAdd(k.cntW, 1ull) - k.baseW] = x;
+}
+
+// Lowers the support of alive edge x by one.
 template <bool TL>
 __device__ __forceinline__ void lower(const PeelArgs& a, Round rd, int32_t x, const Sinks& k,
                                       Tally& tl) {
     ++tl.lowered;
-    const int old = atomicSub(a.s + x, 1);
-    if (old == k.thr) {
-        a.t[x] = -(rd.r + 1);
-        if (is_heavy<TL>(a, x)) k.Hn[atomicAdd(k.cntH, 1ull) - k.baseH] = x;
-        else k.Fn[atomicAdd(k.cntF, 1ull) - k.baseF] = x;
-    }
-    if (old == k.bound) k.Wc[atomicAdd(k.cntW, 1ull) - k.baseW] = x;
+    after_lower<TL>(a, rd, x, atomicSub(a.s + x, 1), k);
 }
 
 // A frontier edge's triangle {e, f, g} whose other two edges are not yet
@@ -221,28 +261,14 @@ __device__ __forceinline__ void destroy(const PeelArgs& a, Round rd, int32_t e, 
 // edge's current support is exactly its number of live triangles (those
 // whose other two edges are not removed): support 0 means nothing to do,
 // and a single-warp group stops once it has seen them all.
-// Lowers the support of x (x >= 0) whose decrement returned old: the
-// crossing checks of lower(), split from the atomic so that a lane can have
-// several decrements in flight.
-__device__ __forceinline__ void after_lower(const PeelArgs& a, Round rd, int32_t x, int old,
-                                            const Sinks& k, bool heavy_x) {
-    if (old == k.thr) {
-        a.t[x] = -(rd.r + 1);
-        if (heavy_x) k.Hn[atomicAdd(k.cntH, 1ull) - k.baseH] = x;
-        else k.Fn[atomicAdd(k.cntF, 1ull) - k.baseF] = x;
-    }
-    if (old == k.bound) k.Wc[atomicAdd(k.cntW, 1ull) - k.baseW] = x;
-}
-
 template <bool TL>
-__device__ __forceinline__ void process_edge(const PeelArgs& a, Round rd, int32_t e,
+__device__ __forceinline__ void process_edge(const PeelArgs& a, Round rd, int32_t e, uint2 rg,
                                              int64_t glane, int64_t gsize, const Sinks& k,
                                              Tally& tl) {
     const bool one_warp = gsize == 32;
     int32_t seen = 0;  // live triangles met so far (one_warp only; warp-uniform)
     if (TL) {
-        // the list range and the support are loaded together
-        const int64_t q0 = (int64_t)a.off[e], q1 = (int64_t)a.off[e + 1];
+        const int64_t q0 = rg.x, q1 = rg.y;
         const int32_t live = ld_cg(a.s + e);
         if (live <= 0) return;
         // PU entries per lane in flight: the pair loads, then both state
@@ -264,7 +290,7 @@ __device__ __forceinline__ void process_edge(const PeelArgs& a, Round rd, int32_
                 tg[u] = v[u] ? ld_cg(a.t + fg[u].y) : 1;
             }
             int32_t xf[PU], xg[PU];
-            int of[PU], og[PU];
+            int of[PU] = {}, og[PU] = {};
             int found = 0;
 #pragma unroll
             for (int u = 0; u < PU; ++u) {
@@ -290,14 +316,9 @@ __device__ __forceinline__ void process_edge(const PeelArgs& a, Round rd, int32_
             }
 #pragma unroll
             for (int u = 0; u < PU; ++u) {
-                if (xf[u] >= 0) {
-                    ++tl.lowered;
-                    after_lower(a, rd, xf[u], of[u], k, is_heavy<TL>(a, xf[u]));
-                }
-                if (xg[u] >= 0) {
-                    ++tl.lowered;
-                    after_lower(a, rd, xg[u], og[u], k, is_heavy<TL>(a, xg[u]));
-                }
+                tl.lowered += (xf[u] >= 0) + (xg[u] >= 0);
+                after_lower<TL>(a, rd, xf[u], of[u], k);
+                after_lower<TL>(a, rd, xg[u], og[u], k);
             }
             if (one_warp) {
                 seen += __reduce_add_sync(0xffffffffu, (unsigned)found);
@@ -362,8 +383,8 @@ __device__ __forceinline__ void process_edge(const PeelArgs& a, Round rd, int32_
 // round-robin.
 template <bool TL>
 __device__ __forceinline__ void process_list(const PeelArgs& a, Round rd, const int32_t* L,
-                                             int64_t nL, int64_t gwarp, int64_t nwarps,
-                                             const Sinks& k, Tally& tl) {
+                                             const uint2* LR, int64_t nL, int64_t gwarp,
+                                             int64_t nwarps, const Sinks& k, Tally& tl) {
     if (nL == 0) return;
     if (TL && nL >= nwarps * LANE_EDGES) {
         // many edges per warp: each lane takes one; lists of up to
@@ -373,14 +394,16 @@ __device__ __forceinline__ void process_list(const PeelArgs& a, Round rd, const 
         for (int64_t base = gwarp * 32; base < nL; base += nwarps * 32) {
             const int64_t j = base + lane;
             const int32_t e = j < nL ? ld_cg(L + j) : -1;
-            const bool longer =
-                e >= 0 && (int64_t)(a.off[e + 1] - a.off[e]) > SHORT_LIST;
-            if (e >= 0 && !longer) process_edge<TL>(a, rd, e, 0, 1, k, tl);
+            const uint2 rg = j < nL ? __ldcg(LR + j) : make_uint2(0, 0);
+            const bool longer = e >= 0 && (int64_t)(rg.y - rg.x) > SHORT_LIST;
+            if (e >= 0 && !longer) process_edge<TL>(a, rd, e, rg, 0, 1, k, tl);
             unsigned rest = __ballot_sync(0xffffffffu, longer);
             while (rest) {
                 const int src = __ffs(rest) - 1;
                 rest &= rest - 1;
-                process_edge<TL>(a, rd, __shfl_sync(0xffffffffu, e, src), lane, 32, k, tl);
+                const uint2 rs = make_uint2(__shfl_sync(0xffffffffu, rg.x, src),
+                                            __shfl_sync(0xffffffffu, rg.y, src));
+                process_edge<TL>(a, rd, __shfl_sync(0xffffffffu, e, src), rs, lane, 32, k, tl);
             }
         }
         return;
@@ -392,7 +415,8 @@ __device__ __forceinline__ void process_list(const PeelArgs& a, Round rd, const 
     if (group >= ngroups) return;
     const int64_t glane = (gwarp % W) * 32 + (threadIdx.x & 31);
     for (int64_t j = group; j < nL; j += ngroups)
-        process_edge<TL>(a, rd, ld_cg(L + j), glane, 32 * W, k, tl);
+        process_edge<TL>(a, rd, ld_cg(L + j), TL ? __ldcg(LR + j) : make_uint2(0, 0), glane,
+                         32 * W, k, tl);
 }
 
 // The peel.  Levels k = k_first, k_first + 1, ...; each level starts with a
@@ -457,6 +481,7 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
                 const int64_t i = base + lane;
                 bool alive = false, win = false, light = false, heavy = false;
                 int32_t e = 0;
+                uint2 rg = make_uint2(0, 0);
                 if (i < n_in) {
                     ++tl.scanned;
                     e = in ? ld_cg(in + i) : (int32_t)i;
@@ -467,15 +492,16 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
                         win = se < bound;
                         if (se < thr) {
                             a.t[e] = -r;
-                            heavy = is_heavy<TL>(a, e);
+                            if (TL) rg = list_range(a, e);
+                            heavy = TL && is_heavy(rg);
                             light = !heavy;
                         }
                     }
                 }
                 if (full) warp_append(alive, e, Aout, &ctl->cntA[pa], baseA[pa]);
                 warp_append(win, e, Wout, &ctl->cntW[wp], baseW[wp]);
-                warp_append(light, e, a.F[fi], &ctl->cntF[pf], baseF[pf]);
-                warp_append(heavy, e, a.H[fi], &ctl->cntH[pf], baseH[pf]);
+                warp_append(light, e, a.F[fi], &ctl->cntF[pf], baseF[pf], a.FR[fi], rg);
+                warp_append(heavy, e, a.H[fi], &ctl->cntH[pf], baseH[pf], a.HR[fi], rg);
             }
             smin = __reduce_min_sync(0xffffffffu, smin);
             if (lane == 0 && smin != INT_MAX) atomicMax(&ctl->minenc[ms], INT_MAX - smin);
@@ -518,10 +544,11 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
             const Round rd{r};
             const int pn = (r + 1) & 1;
             if (leader) a.level_of[r + 1] = k;
-            const Sinks sk{a.F[fi ^ 1], a.H[fi ^ 1], Wout, &ctl->cntF[pn], &ctl->cntH[pn],
-                           &ctl->cntW[wp], baseF[pn], baseH[pn], baseW[wp], thr, bound};
-            process_list<TL>(a, rd, a.F[fi], nF, gwarp, nwarps, sk, tl);
-            process_list<TL>(a, rd, a.H[fi], nH, gwarp, nwarps, sk, tl);
+            const Sinks sk{a.F[fi ^ 1], a.H[fi ^ 1], a.FR[fi ^ 1], a.HR[fi ^ 1], Wout,
+                           &ctl->cntF[pn], &ctl->cntH[pn], &ctl->cntW[wp], baseF[pn],
+                           baseH[pn], baseW[wp], thr, bound};
+            process_list<TL>(a, rd, a.F[fi], a.FR[fi], nF, gwarp, nwarps, sk, tl);
+            process_list<TL>(a, rd, a.H[fi], a.HR[fi], nH, gwarp, nwarps, sk, tl);
             if (!grid_sync(ctl, &epoch, a.spin_ns, &s_ok)) return;
             const unsigned long long eF = ld_vol(&ctl->cntF[pn]), eH = ld_vol(&ctl->cntH[pn]);
             n_alive -= nF + nH;
@@ -797,11 +824,18 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
     }
     if (p.cache) a.s = g->kt_support;
     else TC_TRY(sc.alloc(&a.s, m));
+    // a heavy edge has more than HEAVY of the 3T list entries (the
+    // intersection form has none)
+    const int64_t heavy_cap = p.tl ? std::min<int64_t>(m, 3 * g->triangles / HEAVY + 1) : 1;
     for (int i = 0; i < 2; ++i) {
         TC_TRY(sc.alloc(&a.A[i], m));
         TC_TRY(sc.alloc(&a.W[i], m));
         TC_TRY(sc.alloc(&a.F[i], m));
-        TC_TRY(sc.alloc(&a.H[i], m));
+        TC_TRY(sc.alloc(&a.H[i], heavy_cap));
+        if (p.tl) {
+            TC_TRY(sc.alloc(&a.FR[i], m));
+            TC_TRY(sc.alloc(&a.HR[i], heavy_cap));
+        }
     }
     TC_TRY(sc.alloc(&a.ctl, 1));
     // round numbers live in int32 edge states: at most 2^31 - 16 rounds (a
