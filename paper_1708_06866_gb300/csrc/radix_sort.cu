@@ -20,6 +20,9 @@ namespace {
 
 constexpr int RS_BLOCK = 256;                 // threads per block (== RADIX)
 constexpr int RS_ITEMS = 16;                  // keys per thread
+#ifndef TC_RS_MIN_BLOCKS
+#define TC_RS_MIN_BLOCKS 3                    // resident onesweep blocks per SM (register cap)
+#endif
 constexpr int RS_TILE = RS_BLOCK * RS_ITEMS;  // keys per tile
 constexpr int RS_WARPS = RS_BLOCK / 32;
 constexpr int RADIX = 256;
@@ -28,7 +31,9 @@ constexpr int MAX_PASSES = 8;
 // Status word of (tile, digit): [63:60] pass tag (pass + 1), [59:58] kind
 // (1 = this tile's count, 2 = inclusive prefix through this tile),
 // [57:0] count.  A word whose tag differs from the running pass is "not
-// published yet", so one memset per sort serves every pass.
+// published yet", so one memset per sort serves every pass.  A word carries
+// its whole message, so it is written and polled with relaxed accesses (no
+// fence).
 constexpr uint64_t ST_COUNT_MASK = (1ull << 58) - 1;
 __device__ __forceinline__ uint64_t st_word(int pass, uint64_t kind, uint64_t cnt) {
     return ((uint64_t)(pass + 1) << 60) | (kind << 58) | cnt;
@@ -40,10 +45,21 @@ __global__ void __launch_bounds__(RS_BLOCK) k_histogram(const uint64_t* __restri
     __shared__ uint32_t sh[MAX_PASSES * RADIX];
     for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) sh[i] = 0;
     __syncthreads();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint64_t k = keys[i];
-        for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * RADIX + ((k >> (8 * p)) & 255)], 1u);
+    // HU keys per thread per step, all loaded before the first count
+    constexpr int HU = 8;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * HU;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x * HU + threadIdx.x; b < n; b += stride) {
+        uint64_t k[HU];
+#pragma unroll
+        for (int u = 0; u < HU; ++u) {
+            const int64_t i = b + (int64_t)u * blockDim.x;
+            k[u] = i < n ? keys[i] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < HU; ++u)
+            if (b + (int64_t)u * blockDim.x < n)
+                for (int p = 0; p < passes; ++p)
+                    atomicAdd(&sh[p * RADIX + ((k[u] >> (8 * p)) & 255)], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x)
@@ -63,7 +79,7 @@ __global__ void k_bin_start(unsigned long long* hist) {
 }
 
 template <bool HAS_VAL>
-__global__ void __launch_bounds__(RS_BLOCK) k_onesweep(
+__global__ void __launch_bounds__(RS_BLOCK, TC_RS_MIN_BLOCKS) k_onesweep(
     const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout,
     const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout, int64_t n, int pass,
     const unsigned long long* __restrict__ bin_start, uint64_t* __restrict__ status,
@@ -71,9 +87,11 @@ __global__ void __launch_bounds__(RS_BLOCK) k_onesweep(
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
     uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + RS_TILE);
-    __shared__ uint32_t s_whist[RS_WARPS * RADIX];  // per-warp digit counts, then offsets
-    __shared__ uint32_t s_dstart[RADIX];            // digit start within the sorted tile
-    __shared__ unsigned long long s_gbase[RADIX];   // digit start in the output
+    // per-warp digit counts, then each (warp, digit)'s first position in the
+    // digit-sorted tile
+    __shared__ uint32_t s_whist[RS_WARPS * RADIX];
+    // per digit: output position of tile position p is s_gofs[d] + p
+    __shared__ unsigned long long s_gofs[RADIX];
     __shared__ uint32_t s_scan[33];
     __shared__ int64_t s_tile;
     __shared__ int s_bad;
@@ -89,7 +107,8 @@ __global__ void __launch_bounds__(RS_BLOCK) k_onesweep(
     const int64_t tile = s_tile;
     const int64_t wbase = tile * RS_TILE + (int64_t)warp * (32 * RS_ITEMS);
 
-    // 1. rank every key among the keys of its warp with the same digit
+    // 1. load the warp's keys (all loads in flight before the first match),
+    // then rank every key among the keys of its warp with the same digit
     uint64_t k[RS_ITEMS];
     uint32_t v[RS_ITEMS];
     uint32_t r[RS_ITEMS];
@@ -99,6 +118,10 @@ __global__ void __launch_bounds__(RS_BLOCK) k_onesweep(
         const bool ok = idx < n;
         k[i] = ok ? kin[idx] : 0ull;
         if (HAS_VAL) v[i] = ok ? vin[idx] : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; ++i) {
+        const bool ok = wbase + i * 32 + lane < n;
         const uint32_t d = ok ? (uint32_t)((k[i] >> shift) & 255) : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const int leader = __ffs(peers) - 1;
@@ -123,9 +146,11 @@ __global__ void __launch_bounds__(RS_BLOCK) k_onesweep(
         tot += c;
     }
     uint64_t* my_status = status + tile * RADIX + t;
-    st_release_u64(my_status, st_word(pass, tile == 0 ? 2 : 1, tot));
+    st_relaxed_u64(my_status, st_word(pass, tile == 0 ? 2 : 1, tot));
     uint32_t tile_total;
-    s_dstart[t] = block_exclusive_scan(tot, s_scan, &tile_total);
+    const uint32_t dstart = block_exclusive_scan(tot, s_scan, &tile_total);
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) s_whist[w * RADIX + t] += dstart;
 
     uint64_t prefix = 0;
     if (tile > 0) {
@@ -133,7 +158,7 @@ __global__ void __launch_bounds__(RS_BLOCK) k_onesweep(
         uint64_t t0 = 0;
         bool bad = false;
         for (;;) {
-            const uint64_t st = ld_acquire_u64(status + j * RADIX + t);
+            const uint64_t st = ld_relaxed_u64(status + j * RADIX + t);
             if ((st >> 60) != (uint64_t)(pass + 1)) {
                 const uint64_t now = global_timer_ns();
                 if (t0 == 0) t0 = now;
@@ -148,9 +173,9 @@ __global__ void __launch_bounds__(RS_BLOCK) k_onesweep(
             atomicOr(err, DEV_ERR_TIMEOUT);
             s_bad = 1;
         }
-        st_release_u64(my_status, st_word(pass, 2, prefix + tot));
+        st_relaxed_u64(my_status, st_word(pass, 2, prefix + tot));
     }
-    s_gbase[t] = bin_start[t] + prefix;
+    s_gofs[t] = bin_start[t] + prefix - dstart;  // modulo 2^64: adding p >= dstart is exact
     __syncthreads();
 
     // 3. place keys in digit order within the tile, then write runs out
@@ -159,7 +184,7 @@ __global__ void __launch_bounds__(RS_BLOCK) k_onesweep(
         const int64_t idx = wbase + i * 32 + lane;
         if (idx < n) {
             const uint32_t d = (uint32_t)((k[i] >> shift) & 255);
-            const uint32_t p = s_dstart[d] + s_whist[warp * RADIX + d] + r[i];
+            const uint32_t p = s_whist[warp * RADIX + d] + r[i];
             s_keys[p] = k[i];
             if (HAS_VAL) s_vals[p] = v[i];
         }
@@ -171,7 +196,7 @@ __global__ void __launch_bounds__(RS_BLOCK) k_onesweep(
     for (int p = threadIdx.x; p < tile_n; p += RS_BLOCK) {
         const uint64_t key = s_keys[p];
         const uint32_t d = (uint32_t)((key >> shift) & 255);
-        const unsigned long long pos = s_gbase[d] + (unsigned long long)(p - (int)s_dstart[d]);
+        const unsigned long long pos = s_gofs[d] + (unsigned long long)p;
         if (pos < (unsigned long long)n) {
             kout[pos] = key;
             if (HAS_VAL) vout[pos] = s_vals[p];
