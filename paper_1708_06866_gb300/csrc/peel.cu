@@ -132,8 +132,11 @@ __device__ bool grid_sync(PeelCtl* ctl, unsigned long long* epoch, int64_t spin_
         __threadfence();
         atomicAdd(&ctl->bar, 1ull);
         uint64_t t0 = 0;
-        while (ld_acquire_u64(reinterpret_cast<const uint64_t*>(&ctl->bar)) < target) {
-            if (*(volatile int*)&ctl->abort) {
+        // relaxed polls (one round trip each; the fence after the loop gives
+        // the acquire), the abort flag read every 16th poll
+        for (unsigned polls = 0;
+             ld_relaxed_u64(reinterpret_cast<const uint64_t*>(&ctl->bar)) < target; ++polls) {
+            if ((polls & 15) == 15 && *(volatile int*)&ctl->abort) {
                 ok = 0;
                 break;
             }

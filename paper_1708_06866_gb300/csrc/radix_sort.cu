@@ -3,7 +3,7 @@
 //
 // One histogram pass counts the 8-bit digits of every pass at once; each
 // digit pass is then a single read-and-scatter kernel ("onesweep"): a block
-// ranks its tile of keys by digit with warp match/popc, publishes its digit
+// ranks its tile of keys by digit with warp ballots/popc, publishes its digit
 // counts, and learns the counts of all earlier tiles by a decoupled
 // look-back over a status array.  Every look-back wait is bounded in time;
 // a wait that runs out sets DEV_ERR_TIMEOUT and the block skips its writes.
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(RS_BLOCK, TC_RS_MIN_BLOCKS) k_onesweep(
     const int64_t tile = s_tile;
     const int64_t wbase = tile * RS_TILE + (int64_t)warp * (32 * RS_ITEMS);
 
-    // 1. load the warp's keys (all loads in flight before the first match),
+    // 1. load the warp's keys (all loads in flight before any ranking),
     // then rank every key among the keys of its warp with the same digit
     uint64_t k[RS_ITEMS];
     uint32_t v[RS_ITEMS];
@@ -123,7 +123,16 @@ __global__ void __launch_bounds__(RS_BLOCK, TC_RS_MIN_BLOCKS) k_onesweep(
     for (int i = 0; i < RS_ITEMS; ++i) {
         const bool ok = wbase + i * 32 + lane < n;
         const uint32_t d = ok ? (uint32_t)((k[i] >> shift) & 255) : 256u;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        // lanes with the same digit: one ballot per bit of the 9-bit value
+        // (256 marks a lane past the end; ballots measured faster than
+        // match.any here)
+        unsigned peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < 9; ++b) {
+            const bool bit = (d >> b) & 1u;
+            const unsigned bb = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bb : ~bb;
+        }
         const int leader = __ffs(peers) - 1;
         uint32_t b = 0;
         if (lane == leader && d < 256u) {
