@@ -41,6 +41,16 @@ UNIT = "edges/s"
 CPU_SAMPLE_SCALE = 16   # oracle sample: the same R-MAT generator at scale 16
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# workload's dominant kernel from one ncu capture of this code; an entry is
+# re-taken (or removed) whenever that kernel changes.
+NCU_TRAFFIC = {
+    ("rmat24", "masked product, support"): {
+        "bytes": int(553.1e9 + 75.2e9),
+        "source": "ncu capture, profiles/dram_rmat24_main_kernels.md"},
+}
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -460,6 +470,10 @@ def bench_ours(args, rank, world):
                 "measured" else "fallback",
                 "traffic": None, "algorithmic_bytes_per_launch": dom["bytes_per_launch"],
                 "ms_per_launch": dom["ms_per_launch"]}
+    tr = NCU_TRAFFIC.get((wl.name, dom_name))
+    if tr is not None:
+        roofline["traffic"] = tr["bytes"]
+        roofline["traffic_source"] = tr["source"]
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,

@@ -323,7 +323,7 @@ int batch_run(const tc_batch_desc* d, cudaStream_t user_stream) {
     auto enqueue_query = [&]() -> int {
         if (g.m > 0) {
             TC_TRY(compute_support(&g, g.support, true, nullptr, s, choice.intersect));
-            TC_TRY(to_canonical_i32(g.support, g.fwd, g.m, sup_can, s));
+            TC_TRY(to_canonical_i32(g.support, g.inv, g.m, sup_can, s));
             k_segment_sums<0, int32_t><<<grid_items((int64_t)G * 32), 256, 0, s>>>(sup_can, ge, G,
                                                                                   tri_d);
             TC_LAUNCH_CHECK("k_segment_sums");
@@ -332,7 +332,7 @@ int batch_run(const tc_batch_desc* d, cudaStream_t user_stream) {
         }
         if (peel) {
             TC_TRY(peel_enqueue(plan, s));
-            TC_TRY(mask_from_state(t, g.fwd, g.m, mask_can, s));
+            TC_TRY(mask_from_state(t, g.inv, g.m, mask_can, s));
             k_segment_sums<1, uint8_t><<<grid_items((int64_t)G * 32), 256, 0, s>>>(mask_can, ge, G,
                                                                                   left_d);
             TC_LAUNCH_CHECK("k_segment_sums");

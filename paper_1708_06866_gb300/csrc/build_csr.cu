@@ -236,7 +236,8 @@ __global__ void k_row_stats(const int64_t* __restrict__ rowptr, const int64_t* _
 }
 
 // Internal edge ids: position in the oriented (u, v) order.  fwd[j] is the
-// canonical id of internal edge j; inv is its inverse.
+// canonical id of internal edge j (build time only); inv, kept with the
+// graph, is its inverse.
 __global__ void k_out_degree(const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
                              int32_t n, int32_t* __restrict__ dout) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -341,7 +342,7 @@ int build_graph(Graph* g, const int32_t* src, const int32_t* dst, cudaStream_t s
     TC_TRY(dev_alloc_n(&g->ends, m, s));
     TC_TRY(dev_alloc_n(&g->col, 2 * m, s));
     TC_TRY(dev_alloc_n(&g->eid, 2 * m, s));
-    TC_TRY(dev_alloc_n(&g->fwd, m, s));
+    TC_TRY(dev_alloc_n(&g->inv, m, s));
     {
         Scratch sc(s);
         int32_t *deg, *rank;
@@ -381,21 +382,21 @@ int build_graph(Graph* g, const int32_t* src, const int32_t* dst, cudaStream_t s
             k_upper<<<grid_for(nnz), 256, 0, s>>>(pkeys, nnz, bits, g->upper);
             TC_LAUNCH_CHECK("k_upper");
             int64_t cnt = 0;
-            UpperOp up{pkeys, pvals, bits, g->fwd};
+            int32_t* fwd;  // canonical id of each internal edge
+            TC_TRY(sc.alloc(&fwd, m));
+            UpperOp up{pkeys, pvals, bits, fwd};
             TC_TRY(compact(up, nnz, &cnt, scalar, s));
             if (cnt != m) return fail(TC_ECUDA, "internal: oriented edge count mismatch");
             // renumber edges in oriented order: a row's edges become contiguous,
             // so per-edge arrays indexed by these ids are read and updated with
             // locality (canonical ids are restored at the ABI boundary)
-            int32_t* inv;
             int2* ends2;
-            TC_TRY(sc.alloc(&inv, m));
             TC_TRY(dev_alloc_n(&ends2, m, s));
-            k_invert<<<grid_for(m), 256, 0, s>>>(g->fwd, m, inv);
+            k_invert<<<grid_for(m), 256, 0, s>>>(fwd, m, g->inv);
             TC_LAUNCH_CHECK("k_invert");
-            k_relabel<<<grid_for(nnz), 256, 0, s>>>(g->eid, nnz, inv);
+            k_relabel<<<grid_for(nnz), 256, 0, s>>>(g->eid, nnz, g->inv);
             TC_LAUNCH_CHECK("k_relabel");
-            k_gather_ends<<<grid_for(m), 256, 0, s>>>(g->ends, g->fwd, m, ends2);
+            k_gather_ends<<<grid_for(m), 256, 0, s>>>(g->ends, fwd, m, ends2);
             TC_LAUNCH_CHECK("k_gather_ends");
             dev_free(g->ends, s);
             g->ends = ends2;

@@ -617,20 +617,20 @@ int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangle
 bool triangle_lists_supported(const Graph* g) { return g->max_out <= RX_MAX_OUT; }
 
 namespace {
-__global__ void k_scatter_i32(const int32_t* __restrict__ in, const int32_t* __restrict__ fwd,
-                              int64_t m, int32_t* __restrict__ out) {
+__global__ void k_gather_i32(const int32_t* __restrict__ in, const int32_t* __restrict__ inv,
+                             int64_t m, int32_t* __restrict__ out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
-        out[fwd[j]] = in[j];
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < m; c += stride)
+        out[c] = in[inv[c]];
 }
 }  // namespace
 
-int to_canonical_i32(const int32_t* in, const int32_t* fwd, int64_t m, int32_t* out,
+int to_canonical_i32(const int32_t* in, const int32_t* inv, int64_t m, int32_t* out,
                      cudaStream_t s) {
     if (m == 0) return TC_OK;
-    k_scatter_i32<<<(unsigned)std::min<int64_t>((m + 255) / 256, (int64_t)num_sms() * 16), 256, 0,
-                    s>>>(in, fwd, m, out);
-    TC_LAUNCH_CHECK("k_scatter_i32");
+    k_gather_i32<<<(unsigned)std::min<int64_t>((m + 255) / 256, (int64_t)num_sms() * 16), 256, 0,
+                   s>>>(in, inv, m, out);
+    TC_LAUNCH_CHECK("k_gather_i32");
     return TC_OK;
 }
 

@@ -631,11 +631,11 @@ __global__ void k_peel_init(const int64_t* __restrict__ rowptr, int32_t n,
 // Final states -> canonical-order outputs: the k-truss mask (alive = 0) or
 // truss numbers (an edge removed in a round of level k has truss number k - 1).
 __global__ void k_mask_from_state(const int32_t* __restrict__ t,
-                                  const int32_t* __restrict__ fwd, int64_t m,
+                                  const int32_t* __restrict__ inv, int64_t m,
                                   uint8_t* __restrict__ mask) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
-        mask[fwd[j]] = t[j] == 0 ? 1 : 0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < m; c += stride)
+        mask[c] = t[inv[c]] == 0 ? 1 : 0;
 }
 
 __global__ void k_resume_states(int32_t* __restrict__ t, int64_t m) {
@@ -645,13 +645,13 @@ __global__ void k_resume_states(int32_t* __restrict__ t, int64_t m) {
 }
 
 __global__ void k_truss_from_state(const int32_t* __restrict__ t,
-                                   const int32_t* __restrict__ fwd, int64_t m,
+                                   const int32_t* __restrict__ inv, int64_t m,
                                    const int32_t* __restrict__ level_of,
                                    int32_t* __restrict__ truss) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
-        const int32_t st = t[j];
-        truss[fwd[j]] = st < 0 ? level_of[-st] - 1 : 0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < m; c += stride) {
+        const int32_t st = t[inv[c]];
+        truss[c] = st < 0 ? level_of[-st] - 1 : 0;
     }
 }
 
@@ -895,11 +895,11 @@ int peel_enqueue(PeelPlan* pp, cudaStream_t s) {
     count_launch();
     TC_TRY(p.timer.stop(s));
     if (!p.single && p.out_truss) {
-        k_truss_from_state<<<small_grid(m), 256, 0, s>>>(a.t, g->fwd, m, a.level_of, p.out_truss);
+        k_truss_from_state<<<small_grid(m), 256, 0, s>>>(a.t, g->inv, m, a.level_of, p.out_truss);
         TC_LAUNCH_CHECK("k_truss_from_state");
     }
     if (p.single && p.out_mask) {
-        k_mask_from_state<<<small_grid(m), 256, 0, s>>>(a.t, g->fwd, m, p.out_mask);
+        k_mask_from_state<<<small_grid(m), 256, 0, s>>>(a.t, g->inv, m, p.out_mask);
         TC_LAUNCH_CHECK("k_mask_from_state");
     }
     return TC_OK;
@@ -965,9 +965,9 @@ int run_peel(Graph* g, int32_t k_first, bool single, uint8_t* out_mask, int32_t*
 
 int ensure_support(Graph* g, cudaStream_t s) { return ensure_support_impl(g, s); }
 
-int mask_from_state(const int32_t* t, const int32_t* fwd, int64_t m, uint8_t* mask,
+int mask_from_state(const int32_t* t, const int32_t* inv, int64_t m, uint8_t* mask,
                     cudaStream_t s) {
-    k_mask_from_state<<<small_grid(m), 256, 0, s>>>(t, fwd, m, mask);
+    k_mask_from_state<<<small_grid(m), 256, 0, s>>>(t, inv, m, mask);
     TC_LAUNCH_CHECK("k_mask_from_state");
     return TC_OK;
 }

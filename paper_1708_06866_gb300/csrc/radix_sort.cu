@@ -66,16 +66,22 @@ __global__ void __launch_bounds__(RS_BLOCK) k_histogram(const uint64_t* __restri
         if (sh[i]) atomicAdd(&hist[i], (unsigned long long)sh[i]);
 }
 
-// Per pass: exclusive scan of the digit counts (256 entries, one thread).
-__global__ void k_bin_start(unsigned long long* hist) {
-    if (threadIdx.x != 0) return;
+// Per pass (one block each, a thread per digit): exclusive scan of the digit
+// counts.
+__global__ void __launch_bounds__(RADIX) k_bin_start(unsigned long long* hist) {
+    __shared__ unsigned long long sh[RADIX];
     unsigned long long* h = hist + blockIdx.x * RADIX;
-    unsigned long long run = 0;
-    for (int d = 0; d < RADIX; ++d) {
-        const unsigned long long c = h[d];
-        h[d] = run;
-        run += c;
+    const int d = threadIdx.x;
+    sh[d] = h[d];
+    __syncthreads();
+    // Hillis-Steele inclusive scan in shared memory
+    for (int off = 1; off < RADIX; off <<= 1) {
+        const unsigned long long add = d >= off ? sh[d - off] : 0ull;
+        __syncthreads();
+        sh[d] += add;
+        __syncthreads();
     }
+    h[d] = d == 0 ? 0ull : sh[d - 1];
 }
 
 template <bool HAS_VAL>
@@ -263,7 +269,7 @@ int radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t*
     const int hblocks = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * 4);
     k_histogram<<<hblocks, RS_BLOCK, 0, s>>>(keys, n, passes, hist);
     TC_LAUNCH_CHECK("k_histogram");
-    k_bin_start<<<passes, 32, 0, s>>>(hist);
+    k_bin_start<<<passes, RADIX, 0, s>>>(hist);
     TC_LAUNCH_CHECK("k_bin_start");
 
     const bool has_val = vals != nullptr;
@@ -391,7 +397,7 @@ extern "C" int tc_sort_keys_static(uint64_t* keys, int64_t n, int32_t key_bits,
     const int hblocks = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * 4);
     k_histogram<<<hblocks, RS_BLOCK, 0, s>>>(keys, n, passes, hist);
     TC_LAUNCH_CHECK("k_histogram");
-    k_bin_start<<<passes, 32, 0, s>>>(hist);
+    k_bin_start<<<passes, RADIX, 0, s>>>(hist);
     TC_LAUNCH_CHECK("k_bin_start");
     const int64_t spin = spin_limit_ns();
     uint64_t *ka = keys, *kb = alt;

@@ -106,7 +106,7 @@ void free_graph(Graph* g) {
     dev_free(g->upper, s);
     dev_free(g->col, s);
     dev_free(g->eid, s);
-    dev_free(g->fwd, s);
+    dev_free(g->inv, s);
     dev_free(g->oshift, s);
     dev_free(g->support, s);
     dev_free(g->tri_off, s);
@@ -260,11 +260,11 @@ int tc_edge_support(tc_graph* g, int32_t* support_out, int64_t* triangles_out,
     // the cached supports are in internal edge order: scatter to edge ids
     if (gg->m == 0) return TC_OK;
     if (!tc::is_host_pointer(support_out))
-        return tc::to_canonical_i32(gg->support, gg->fwd, gg->m, support_out, s);
+        return tc::to_canonical_i32(gg->support, gg->inv, gg->m, support_out, s);
     tc::Scratch sc(s);
     int32_t* tmp;
     TC_TRY(sc.alloc(&tmp, gg->m));
-    TC_TRY(tc::to_canonical_i32(gg->support, gg->fwd, gg->m, tmp, s));
+    TC_TRY(tc::to_canonical_i32(gg->support, gg->inv, gg->m, tmp, s));
     return deliver(support_out, tmp, gg->m, s);
 }
 
@@ -351,7 +351,8 @@ int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream) {
     info->max_out = gg->max_out;
     info->wedge_work = ww;
     const int64_t m = gg->m, n = gg->n;
-    info->device_bytes = m * (4 + 4 + 8 + 4 + 4 + 4) + 8 * (n + 1) + 8 * n + 8 * n +
+    // lo, hi, ends, inv (m each) and col, eid (2m each); rowptr, upper, oshift
+    info->device_bytes = m * (4 + 4 + 8 + 4 + 8 + 8) + 8 * (n + 1) + 8 * n + 8 * n +
                          (gg->support ? 4 * m : 0) +
                          (gg->tri_valid ? 8 * (m + 1) + 24 * gg->triangles : 0) +
                          (gg->kt_state ? 8 * m : 0) + (gg->truss_cache ? 4 * m : 0) + (gg->kt_col ? 16 * m + 4 * n : 0);

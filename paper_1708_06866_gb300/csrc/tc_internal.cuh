@@ -229,8 +229,8 @@ struct Graph {
     int32_t* lo = nullptr;
     int32_t* hi = nullptr;
     // Internal edge ids: j = position in the oriented (u, v) order, u < v in
-    // rank; fwd[j] is its canonical id (the ABI's edge id).  Everything below
-    // that is per edge is in internal order.
+    // rank; inv[c] is the internal id of canonical edge c (the ABI's edge
+    // id).  Everything below that is per edge is in internal order.
     // endpoints in rank ids, (u, v), internal order
     int2* ends = nullptr;
     // symmetric CSR over rank ids: row r = [rowptr[r], rowptr[r+1]); its part
@@ -239,7 +239,7 @@ struct Graph {
     int64_t* upper = nullptr;
     int32_t* col = nullptr;   // 2m neighbour rank ids
     int32_t* eid = nullptr;   // 2m internal edge ids
-    int32_t* fwd = nullptr;   // canonical id of each internal edge
+    int32_t* inv = nullptr;   // internal id of each canonical edge
     // internal ids follow the out-lists: the out-entry at position p of row r
     // is edge p - oshift[r] (n entries)
     int64_t* oshift = nullptr;
@@ -319,11 +319,12 @@ int peel_enqueue(PeelPlan* p, cudaStream_t s);
 int peel_finish(PeelPlan* p, cudaStream_t s, int64_t* n_alive, int32_t* kmax);
 bool peel_uses_lists(const PeelPlan* p);
 int ensure_support(Graph* g, cudaStream_t s);
-// Internal-order per-edge arrays -> canonical order (out[fwd[j]] = in[j]).
-int to_canonical_i32(const int32_t* in, const int32_t* fwd, int64_t m, int32_t* out,
+// Internal-order per-edge arrays -> canonical order (out[c] = in[inv[c]]: a
+// gather, so the writes are coalesced).
+int to_canonical_i32(const int32_t* in, const int32_t* inv, int64_t m, int32_t* out,
                      cudaStream_t s);
 // k-truss mask in canonical order from internal edge states (alive = 0).
-int mask_from_state(const int32_t* t, const int32_t* fwd, int64_t m, uint8_t* mask,
+int mask_from_state(const int32_t* t, const int32_t* inv, int64_t m, uint8_t* mask,
                     cudaStream_t s);
 
 int build_graph(Graph* g, const int32_t* src_d, const int32_t* dst_d, cudaStream_t s);
