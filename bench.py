@@ -45,6 +45,9 @@ CPU_SAMPLE_SCALE = 16   # oracle sample: the same R-MAT generator at scale 16
 # workload's dominant kernel from one ncu capture of this code; an entry is
 # re-taken (or removed) whenever that kernel changes.
 NCU_TRAFFIC = {
+    ("rmat20", "peel (k_peel)"): {
+        "bytes": int(16.233e9 + 1.900e9),
+        "source": "ncu capture, profiles/dram_rmat20_main_kernels.md"},
     ("rmat24", "masked product, support"): {
         "bytes": int(553.1e9 + 75.2e9),
         "source": "ncu capture, profiles/dram_rmat24_main_kernels.md"},
