@@ -257,7 +257,7 @@ int tc_edge_support(tc_graph* g, int32_t* support_out, int64_t* triangles_out,
         gg->support_valid = true;
     }
     if (triangles_out) *triangles_out = gg->triangles;
-    // the cached supports are in internal edge order: scatter to edge ids
+    // the cached supports are in internal edge order: gather them by edge id
     if (gg->m == 0) return TC_OK;
     if (!tc::is_host_pointer(support_out))
         return tc::to_canonical_i32(gg->support, gg->inv, gg->m, support_out, s);
