@@ -57,3 +57,24 @@ def test_reference_arm_only_rank0_reports(monkeypatch):
     class A:
         steps, warmup, workload = 1, 0, "rmat20"
     assert bench.bench_reference(A(), rank=1, world=2) is None
+
+
+def test_ncu_traffic_entries_name_a_workload_a_kernel_and_a_capture():
+    """Each DRAM-traffic figure the bench reports names a timed workload, a
+    kernel the bench times, and a committed capture summary that states the
+    same read and write bytes."""
+    import re
+    import graphgen
+    kernels = {"masked product, count", "masked product, support", "triangle lists",
+               "peel (k_peel)"}
+    assert bench.NCU_TRAFFIC
+    for (workload, kernel), entry in bench.NCU_TRAFFIC.items():
+        assert workload in graphgen.WORKLOADS
+        assert kernel in kernels
+        path = re.search(r"profiles/\S+\.md", entry["source"]).group(0)
+        text = open(os.path.join(ROOT, path)).read()
+        gb = [float(x) for x in re.findall(r"(\d+\.\d+) GB", text)]
+        # some row of the summary holds the read and write figures that sum
+        # to the reported bytes (to the summary's rounding)
+        assert any(abs((a + b) * 1e9 - entry["bytes"]) < 0.02e9 * max(1.0, (a + b) / 10)
+                   for a, b in zip(gb, gb[1:])), (workload, kernel)
