@@ -851,10 +851,13 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
         }
     }
     TC_TRY(sc.alloc(&a.ctl, 1));
-    // round numbers live in int32 edge states: at most 2^31 - 16 rounds (a
-    // round removes at least one edge, so m + levels bounds them; the kernel
-    // stops with an overflow status if the table ever runs out)
-    a.max_round = std::min<int64_t>(2 * m + 16, 0x7fffffffLL - 16);
+    // round numbers live in int32 edge states: at most 2^31 - 16 rounds.  A
+    // non-empty round removes at least one edge (at most m of them) and a
+    // level takes one more number for its scan; levels end at k <= the
+    // largest support + 3 <= max degree + 2, so there are at most max degree
+    // + 1 of them.  The kernel stops with an overflow status if the table
+    // ever runs out.
+    a.max_round = std::min<int64_t>(m + 2 * (int64_t)g->max_deg + 64, 0x7fffffffLL - 16);
     TC_TRY(sc.alloc(&a.level_of, a.max_round));
     p.fn = p.tl ? (const void*)k_peel<true> : (const void*)k_peel<false>;
     int per_sm = 0;

@@ -68,7 +68,8 @@ struct tc_server {
 
     int64_t estimate(int32_t gid) const {
         // CSR and edge arrays (~40 B per input pair), a call's scratch
-        // (~60 B), and the optional memory the graph may keep
+        // (at most ~56 B: the peel's lists of edges, frontier ranges and
+        // round table), and the optional memory the graph may keep
         return (100 + opt_per_pair) * src[gid].m_in + (1 << 20);
     }
 };
