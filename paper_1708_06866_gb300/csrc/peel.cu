@@ -268,10 +268,11 @@ __device__ __forceinline__ void destroy(const PeelArgs& a, Round rd, int32_t e, 
     if (rd.alive(tg)) lower<TL>(a, rd, g, k, tl);
 }
 
-// All triangles through frontier edge e, by a group of gsize lanes.  The
-// edge's current support is exactly its number of live triangles (those
-// whose other two edges are not removed): support 0 means nothing to do,
-// and a single-warp group stops once it has seen them all.
+// All triangles through frontier edge e, by a group of gsize lanes (rg: its
+// triangle-list range, list form only).  The edge's current support is
+// exactly its number of live triangles (those whose other two edges are not
+// removed): support 0 means nothing to do, and a single-warp group stops
+// once it has seen them all.
 template <bool TL>
 __device__ __forceinline__ void process_edge(const PeelArgs& a, Round rd, int32_t e, uint2 rg,
                                              int64_t glane, int64_t gsize, const Sinks& k,
