@@ -7,9 +7,10 @@
 // phase — supports (Algorithm 4's s), per-graph triangle counts (Section
 // III-A), the k-truss peel (Section III-B) and per-graph truss sizes — is one
 // launch over all graphs.  The query phase can be captured into one CUDA
-// graph and launched once.  An autotuner picks the masked-product kernel and
-// the peel form by timing both on the batch, and caches the choice by a
-// signature of the union graph's size and degree classes.
+// graph and launched once.  An autotuner picks the masked-product kernel,
+// the peel form and the peel's grid size by timing them on the batch, and
+// caches the choice by a signature of the union graph's size and degree
+// classes.
 #include <algorithm>
 #include <map>
 #include <mutex>
