@@ -356,9 +356,10 @@ int64_t tc_launch_count(void);
  * if k >= 2, per-graph k-truss sizes (Section III-B) with one launch per
  * phase over all graphs.  With use_graph = 1 the query phase (supports,
  * per-graph sums, the peel) is captured into one CUDA graph and launched
- * once.  The first batch with a given size/degree signature times both
- * masked-product kernels and both peel forms on the batch and keeps the
- * fastest; later batches with that signature reuse the choice.
+ * once.  The first batch with a given size/degree signature times the
+ * masked-product kernels, and both peel forms at three grid sizes, on the
+ * batch and keeps the fastest; later batches with that signature reuse the
+ * choice.
  */
 typedef struct {
     int64_t build_ns;          /* union build, CUDA events on the call's stream */
