@@ -13,7 +13,12 @@ never needs:
   * level skipping: when a level's scan finds no edge below k - 2, the levels
     up to (smallest surviving support) + 2 remove nothing, so the next level
     to peel is that support + 3;
-  * the truss number of an edge removed while peeling level k is k - 1.
+  * the truss number of an edge removed while peeling level k is k - 1;
+  * windowed scans: a full scan (of the alive edges) also collects the
+    "window" of alive edges with support below thr + WINDOW; the next levels
+    scan only the window, which gains every edge whose support falls to just
+    below the window bound during a round, and the level-skipping minimum of
+    a windowed scan is capped at the bound.
 
 This file states those rules as a slow model (no code shared with the CUDA
 path or the oracle) and checks, on small graphs, that after every round each
@@ -145,3 +150,71 @@ def test_dropping_the_ownership_rule_is_caught():
     bulk_peel(tri, 3, single=False)
     with pytest.raises(AssertionError):
         bulk_peel(tri, 3, single=False, owner_rule=False)
+
+
+def windowed_peel(tri, window):
+    """The decomposition with the device's scan structure: full scans that
+    collect the alive list and the window, windowed scans in between.  At
+    every scan the frontier found must equal the one a scan of all alive
+    edges finds.  Returns the truss numbers."""
+    m = len(tri)
+    s = [len(t) for t in tri]
+    removed = [False] * m
+    truss = [0] * m
+    k, bound = 3, None
+    alive_list = list(range(m))
+    win = []
+    while not all(removed):
+        thr = k - 2
+        full = bound is None or thr > bound
+        if full:
+            bound = thr + window
+        scan = alive_list if full else win
+        scanned = [e for e in scan if not removed[e]]
+        if full:
+            alive_list = scanned
+        next_win = [e for e in scanned if s[e] < bound]
+        frontier = [e for e in scanned if s[e] < thr]
+        truth = [e for e in range(m) if not removed[e] and s[e] < thr]
+        assert sorted(frontier) == truth, (k, full)
+        if not frontier:
+            m0 = min(s[e] for e in scanned) if scanned else bound
+            if not full:
+                m0 = min(m0, bound)   # edges outside the window have s >= bound
+            k = max(k + 1, m0 + 3)
+            win = next_win
+            continue
+        while frontier:
+            dying = set(frontier)
+            lowered = []
+            for e in frontier:
+                for f, g in tri[e]:
+                    if (removed[f] and f not in dying) or (removed[g] and g not in dying):
+                        continue
+                    if min(x for x in (e, f, g) if x in dying) != e:
+                        continue
+                    for x in (f, g):
+                        if x not in dying and not removed[x]:
+                            old = s[x]
+                            s[x] -= 1
+                            if old == bound:
+                                next_win.append(x)   # just fell below the window bound
+                            if old == thr:
+                                lowered.append(x)    # just fell below the threshold
+            for e in frontier:
+                removed[e] = True
+                truss[e] = k - 1
+            frontier = sorted(lowered)
+        win = next_win
+        k += 1
+    return np.array(truss, dtype=np.int32)
+
+
+@pytest.mark.parametrize("window", [1, 2, 3, 16])
+@pytest.mark.parametrize("name,g", list(graphs()), ids=[n for n, _ in graphs()])
+def test_windowed_scans_find_every_frontier(name, g, window):
+    src, dst, n = g
+    og = oracle.OracleGraph.from_edges(src, dst, n)
+    lo, hi = oracle.canonical_edges(src, dst, n)
+    truss = windowed_peel(triangles_of_edges(n, lo, hi), window)
+    assert np.array_equal(truss, og.truss_decomposition()[1]), (name, window)
