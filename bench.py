@@ -9,10 +9,12 @@ for the scale-24 workload, the k-trusses at k = 3, 4, 6, 8 (ktruss).  The
 rate is undirected edges after cleaning / step time (the paper's "rate",
 Section IV).
 
-Default workload: R-MAT scale 20, edgefactor 16, a/b/c/d = .57/.19/.19/.05,
-vertices permuted, seed 1, full decomposition k = 3..kmax.
+Default workload: R-MAT scale 24 (268,435,456 generated edges), edgefactor
+16, a/b/c/d = .57/.19/.19/.05, vertices permuted, seed 2: count, supports
+and the k-trusses at k = 3, 4, 6, 8 — the largest single-GPU configuration.
+rmat20 (scale 20, full decomposition k = 3..kmax) stays selectable.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat20|rmat24|er4096]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat24|rmat20|er4096|...]
   python bench.py --impl reference ...     # the CPU oracle on a bounded sample
 
 Under torchrun (N > 1) every rank runs an independent replica on its own GPU
@@ -42,16 +44,57 @@ CPU_SAMPLE_SCALE = 16   # oracle sample: the same R-MAT generator at scale 16
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
-# workload's dominant kernel from one ncu capture of this code; an entry is
-# re-taken (or removed) whenever that kernel changes.
-NCU_TRAFFIC = {
-    ("rmat20", "peel (k_peel)"): {
-        "bytes": int(16.231e9 + 1.899e9),
-        "source": "ncu capture, profiles/dram_rmat20_main_kernels.md"},
-    ("rmat24", "masked product, support"): {
-        "bytes": int(552.972e9 + 75.158e9),
-        "source": "ncu capture, profiles/dram_rmat24_main_kernels.md"},
+# workload's dominant kernel from one ncu capture, with the SHA-256 of the
+# kernel's source file at capture time.  The bench reports the bytes only
+# while that file is unchanged (otherwise traffic is null: the counters no
+# longer describe the kernel that ran).
+NCU_TRAFFIC = {}
+
+KERNEL_SOURCE = {
+    "masked product, count": "intersect.cu",
+    "masked product, support": "intersect.cu",
+    "triangle lists": "intersect.cu",
+    "peel (k_peel)": "peel.cu",
 }
+
+
+def kernel_source_sha(name):
+    import hashlib
+    f = KERNEL_SOURCE.get(name)
+    if f is None:
+        return None
+    path = os.path.join(ROOT, "paper_1708_06866_gb300", "csrc", f)
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()
+
+
+def ncu_traffic(workload, kernel):
+    """The captured DRAM bytes of this kernel on this workload, if the capture
+    was taken of the source that is built now; else None."""
+    tr = NCU_TRAFFIC.get((workload, kernel))
+    if tr is None or tr.get("source_sha256") != kernel_source_sha(kernel):
+        return None
+    return tr
+
+
+def oracle_fixture(workload):
+    """The stored oracle run of a whole workload (written by
+    tests/golden/make_oracle_fixtures.py): its edge count and wall time."""
+    path = os.path.join(ROOT, "tests", "golden", f"{workload}_oracle.txt")
+    if not os.path.exists(path):
+        return None
+    m = wall = None
+    with open(path) as f:
+        for ln in f:
+            if ln.startswith("m "):
+                m = int(ln.split()[1])
+            elif ln.startswith("# oracle wall time"):
+                wall = float(ln.split()[4])
+    if not m or not wall:
+        return None
+    return {"edges": m, "wall_s": wall, "edges_per_s": m / wall,
+            "source": f"tests/golden/{workload}_oracle.txt (one oracle run of the whole "
+                      f"workload on the host that wrote the fixture)"}
 
 
 def load_peaks():
@@ -473,7 +516,7 @@ def bench_ours(args, rank, world):
                 "measured" else "fallback",
                 "traffic": None, "algorithmic_bytes_per_launch": dom["bytes_per_launch"],
                 "ms_per_launch": dom["ms_per_launch"]}
-    tr = NCU_TRAFFIC.get((wl.name, dom_name))
+    tr = ncu_traffic(wl.name, dom_name)
     if tr is not None:
         roofline["traffic"] = tr["bytes"]
         roofline["traffic_source"] = tr["source"]
@@ -504,7 +547,7 @@ def bench_ours(args, rank, world):
                          "sms": torch.cuda.get_device_properties(local).multi_processor_count}}
 
     if not args.no_e2e:
-        out["e2e"] = bench_e2e(args, tc, torch, src_h, dst_h, n, wl, stream)
+        out["e2e"] = bench_e2e(args, tc, torch, src_h, dst_h, n, wl, stream, flush)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -513,9 +556,10 @@ def bench_ours(args, rank, world):
     return out
 
 
-def bench_e2e(args, tc, torch, src_h, dst_h, n, wl, stream):
+def bench_e2e(args, tc, torch, src_h, dst_h, n, wl, stream, flush):
     """Same metric through the public API with host buffers: pinned host
-    inputs copied in and per-edge results read back inside the timed region."""
+    inputs copied in and per-edge results read back inside the timed region.
+    Same step count and L2 flush between steps as the device-resident timing."""
     src_p = torch.from_numpy(src_h).pin_memory()
     dst_p = torch.from_numpy(dst_h).pin_memory()
     g = tc.tc_build_csr(src_p, dst_p, n, stream=stream)
@@ -530,19 +574,23 @@ def bench_e2e(args, tc, torch, src_h, dst_h, n, wl, stream):
     elif wl.name != "er4096":
         outs["truss"] = torch.empty(m, dtype=torch.int32).pin_memory()
         d2h += 4 * m + 4
-    steps = max(1, min(args.steps, 3))
+    steps = args.steps
+    total = 0.0
     with torch.cuda.stream(stream):
         run_step(tc, torch, src_p, dst_p, n, wl, stream, outs=outs)
         torch.cuda.synchronize()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
         for _ in range(steps):
+            flush.fill_(1)          # evict L2 between steps (outside the events)
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
             run_step(tc, torch, src_p, dst_p, n, wl, stream, outs=outs)
-        t1.record(stream)
-        torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1) / steps
-    return {"value": m / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            t1.record(stream)
+            torch.cuda.synchronize()
+            total += t0.elapsed_time(t1)
+    ms = total / steps
+    return {"value": m / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "l2": f"flushed between steps ({args.flush_mb} MB write)",
             "h2d_bytes_per_step": int(src_h.nbytes + dst_h.nbytes),
             "d2h_bytes_per_step": int(d2h + 8)}
 
@@ -594,11 +642,17 @@ def cpu_baseline(wl, reps=2):
         m, dt = oracle_sample_step(wl)
         ms += m
         ts += dt
-    return {"value": ms / ts, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
-            "sample": f"oracle (serial peel; count/support loops OpenMP) on {oracle_sample_name(wl)}, whole path "
-                      f"(cleaning + count + support + full truss decomposition), {reps} runs, "
-                      f"{ts:.1f} s" + ("" if wl.family == "er" else
-                                       f"; the {wl.name} workload itself is larger")}
+    out = {"value": ms / ts, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
+           "sample": f"oracle (serial peel; count/support loops OpenMP) on {oracle_sample_name(wl)}, whole path "
+                     f"(cleaning + count + support + full truss decomposition), {reps} runs, "
+                     f"{ts:.1f} s" + ("" if wl.family == "er" else
+                                      f"; the {wl.name} workload itself is larger")}
+    full = oracle_fixture(wl.name)
+    if full is not None:
+        # the oracle on the whole workload (too slow to rerun here): its
+        # serial peel makes it far slower per edge than on the sample
+        out["full_workload"] = full
+    return out
 
 
 def bench_reference(args, rank, world):
@@ -632,7 +686,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(graphgen.WORKLOADS) + ["batch10k", "serve"],
-                    default="rmat20")
+                    default="rmat24")
     ap.add_argument("--batch-graphs", type=int, default=10_000)
     ap.add_argument("--batch-sample", type=int, default=300)
     ap.add_argument("--serve-slots", type=int, default=8)

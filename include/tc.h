@@ -409,7 +409,9 @@ int tc_batch_run(const tc_batch_desc* d, void* cuda_stream);
  * process exits.  Limit: n <= TC_SORT_STATIC_MAX_KEYS (2^20); larger n
  * returns TC_EOVERFLOW without touching the keys.
  * keys: device memory of the caller, n entries (host pointers: TC_EINVAL).
- * key_bits: 1..64; bits above key_bits are ignored by the ordering.
+ * key_bits: 1..64; bits above key_bits are ignored by the ordering (the
+ * last digit pass masks them), and keys equal in their low key_bits bits
+ * keep their input order (the sort is stable).
  * The first call on a device sets the array up (looks up its device address
  * and sets a kernel attribute) with that device current: make that first
  * call before any stream capture.  Every call shares the one array and the

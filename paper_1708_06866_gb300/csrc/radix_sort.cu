@@ -39,8 +39,16 @@ __device__ __forceinline__ uint64_t st_word(int pass, uint64_t kind, uint64_t cn
     return ((uint64_t)(pass + 1) << 60) | (kind << 58) | cnt;
 }
 
+// Digit mask of pass p for keys of key_bits bits: the last pass of a
+// key_bits that is not a multiple of 8 keeps only the bits below key_bits,
+// so higher bits never take part in the ordering.
+__host__ __device__ __forceinline__ uint32_t digit_mask(int p, int key_bits) {
+    const int rem = key_bits - 8 * p;
+    return rem >= 8 ? 255u : (1u << rem) - 1u;
+}
+
 __global__ void __launch_bounds__(RS_BLOCK) k_histogram(const uint64_t* __restrict__ keys,
-                                                        int64_t n, int passes,
+                                                        int64_t n, int passes, int key_bits,
                                                         unsigned long long* __restrict__ hist) {
     __shared__ uint32_t sh[MAX_PASSES * RADIX];
     for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) sh[i] = 0;
@@ -59,7 +67,7 @@ __global__ void __launch_bounds__(RS_BLOCK) k_histogram(const uint64_t* __restri
         for (int u = 0; u < HU; ++u)
             if (b + (int64_t)u * blockDim.x < n)
                 for (int p = 0; p < passes; ++p)
-                    atomicAdd(&sh[p * RADIX + ((k[u] >> (8 * p)) & 255)], 1u);
+                    atomicAdd(&sh[p * RADIX + ((k[u] >> (8 * p)) & digit_mask(p, key_bits))], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x)
@@ -87,7 +95,7 @@ __global__ void __launch_bounds__(RADIX) k_bin_start(unsigned long long* hist) {
 template <bool HAS_VAL>
 __global__ void __launch_bounds__(RS_BLOCK, TC_RS_MIN_BLOCKS) k_onesweep(
     const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout,
-    const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout, int64_t n, int pass,
+    const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout, int64_t n, int pass, uint32_t dmask,
     const unsigned long long* __restrict__ bin_start, uint64_t* __restrict__ status,
     unsigned int* __restrict__ tile_counter, int* __restrict__ err, int64_t spin_ns) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -128,7 +136,7 @@ __global__ void __launch_bounds__(RS_BLOCK, TC_RS_MIN_BLOCKS) k_onesweep(
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; ++i) {
         const bool ok = wbase + i * 32 + lane < n;
-        const uint32_t d = ok ? (uint32_t)((k[i] >> shift) & 255) : 256u;
+        const uint32_t d = ok ? (uint32_t)((k[i] >> shift) & dmask) : 256u;
         // lanes with the same digit: one ballot per bit of the 9-bit value
         // (256 marks a lane past the end; ballots measured faster than
         // match.any here)
@@ -198,7 +206,7 @@ __global__ void __launch_bounds__(RS_BLOCK, TC_RS_MIN_BLOCKS) k_onesweep(
     for (int i = 0; i < RS_ITEMS; ++i) {
         const int64_t idx = wbase + i * 32 + lane;
         if (idx < n) {
-            const uint32_t d = (uint32_t)((k[i] >> shift) & 255);
+            const uint32_t d = (uint32_t)((k[i] >> shift) & dmask);
             const uint32_t p = s_whist[warp * RADIX + d] + r[i];
             s_keys[p] = k[i];
             if (HAS_VAL) s_vals[p] = v[i];
@@ -210,7 +218,7 @@ __global__ void __launch_bounds__(RS_BLOCK, TC_RS_MIN_BLOCKS) k_onesweep(
     const int tile_n = rem < RS_TILE ? (int)rem : RS_TILE;
     for (int p = threadIdx.x; p < tile_n; p += RS_BLOCK) {
         const uint64_t key = s_keys[p];
-        const uint32_t d = (uint32_t)((key >> shift) & 255);
+        const uint32_t d = (uint32_t)((key >> shift) & dmask);
         const unsigned long long pos = s_gofs[d] + (unsigned long long)p;
         if (pos < (unsigned long long)n) {
             kout[pos] = key;
@@ -267,7 +275,7 @@ int radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t*
     TC_CUDA_TRY(cudaMemsetAsync(counters, 0, sizeof(unsigned int) * MAX_PASSES, s));
 
     const int hblocks = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * 4);
-    k_histogram<<<hblocks, RS_BLOCK, 0, s>>>(keys, n, passes, hist);
+    k_histogram<<<hblocks, RS_BLOCK, 0, s>>>(keys, n, passes, key_bits, hist);
     TC_LAUNCH_CHECK("k_histogram");
     k_bin_start<<<passes, RADIX, 0, s>>>(hist);
     TC_LAUNCH_CHECK("k_bin_start");
@@ -293,11 +301,12 @@ int radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t*
     for (int p = 0; p < passes; ++p) {
         if (has_val)
             k_onesweep<true><<<(unsigned)tiles, RS_BLOCK, dyn_smem(true), s>>>(
-                ka, kb, va, vb, n, p, hist + p * RADIX, status, counters + p, dev_err, spin);
+                ka, kb, va, vb, n, p, digit_mask(p, key_bits), hist + p * RADIX, status,
+                counters + p, dev_err, spin);
         else
             k_onesweep<false><<<(unsigned)tiles, RS_BLOCK, dyn_smem(false), s>>>(
-                ka, kb, nullptr, nullptr, n, p, hist + p * RADIX, status, counters + p, dev_err,
-                spin);
+                ka, kb, nullptr, nullptr, n, p, digit_mask(p, key_bits), hist + p * RADIX,
+                status, counters + p, dev_err, spin);
         TC_LAUNCH_CHECK("k_onesweep");
         std::swap(ka, kb);
         std::swap(va, vb);
@@ -395,7 +404,7 @@ extern "C" int tc_sort_keys_static(uint64_t* keys, int64_t n, int32_t key_bits,
     TC_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(uint64_t) * tiles * RADIX, s));
     TC_CUDA_TRY(cudaMemsetAsync(counters, 0, kCtlBytes, s));
     const int hblocks = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * 4);
-    k_histogram<<<hblocks, RS_BLOCK, 0, s>>>(keys, n, passes, hist);
+    k_histogram<<<hblocks, RS_BLOCK, 0, s>>>(keys, n, passes, key_bits, hist);
     TC_LAUNCH_CHECK("k_histogram");
     k_bin_start<<<passes, RADIX, 0, s>>>(hist);
     TC_LAUNCH_CHECK("k_bin_start");
@@ -403,7 +412,8 @@ extern "C" int tc_sort_keys_static(uint64_t* keys, int64_t n, int32_t key_bits,
     uint64_t *ka = keys, *kb = alt;
     for (int p = 0; p < passes; ++p) {
         k_onesweep<false><<<(unsigned)tiles, RS_BLOCK, dyn_smem(false), s>>>(
-            ka, kb, nullptr, nullptr, n, p, hist + p * RADIX, status, counters + p, err, spin);
+            ka, kb, nullptr, nullptr, n, p, digit_mask(p, key_bits), hist + p * RADIX, status,
+            counters + p, err, spin);
         TC_LAUNCH_CHECK("k_onesweep");
         std::swap(ka, kb);
     }

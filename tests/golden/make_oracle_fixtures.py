@@ -3,7 +3,9 @@
 Calls only the oracle (and the seeded generators that feed it).  Usage:
     python tests/golden/make_oracle_fixtures.py rmat20 [--truss]
 writes tests/golden/<name>_oracle.txt.  Hashes are SHA-256 of the little-endian
-int32 arrays in canonical edge order.
+int32 arrays in canonical edge order.  While it runs, the lines found so far
+are kept in <name>_oracle.txt.partial (a scale-24 run takes hours), with the
+time each step finished; the finished file replaces it at the end.
 """
 import argparse
 import hashlib
@@ -34,20 +36,31 @@ def main():
     s, d, n = w.generate()
     lines = [f"# oracle results for workload {w.name}: {w.description}",
              "# written by tests/golden/make_oracle_fixtures.py (oracle only)"]
+    out = os.path.join(HERE, f"{w.name}_oracle.txt")
     t0 = time.time()
+
+    def checkpoint():
+        with open(out + ".partial", "w") as f:
+            f.write("\n".join(lines) + f"\n# partial, {time.time() - t0:.1f} s so far\n")
+        print(lines[-1], f"({time.time() - t0:.1f} s)", flush=True)
+
     g = oracle.OracleGraph.from_edges(s, d, n)
     lines.append(f"n {n}")
     lines.append(f"m_in {len(s)}")
     lines.append(f"m {g.m}")
     lines.append(f"lo_hi_sha256 {sha(g.lo)} {sha(g.hi)}")
+    checkpoint()
     T = g.count()
     lines.append(f"triangles {T}")
+    checkpoint()
     sup = g.support()
     lines.append(f"support_sha256 {sha(sup)}")
     lines.append(f"support_sum {int(sup.sum(dtype=np.int64))}")
+    checkpoint()
     for k in [int(x) for x in args.ks.split(",") if x]:
         mask, _, left = g.ktruss(k)
         lines.append(f"ktruss {k} {left} {sha(mask.astype(np.int32))}")
+        checkpoint()
     if args.truss:
         kmax, t = g.truss_decomposition()
         lines.append(f"kmax {kmax}")
@@ -55,9 +68,10 @@ def main():
         counts = [int((t >= k).sum()) for k in range(2, kmax + 2)]
         lines.append("truss_edges_from_k2 " + " ".join(map(str, counts)))
     lines.append(f"# oracle wall time {time.time() - t0:.1f} s")
-    out = os.path.join(HERE, f"{w.name}_oracle.txt")
     with open(out, "w") as f:
         f.write("\n".join(lines) + "\n")
+    if os.path.exists(out + ".partial"):
+        os.remove(out + ".partial")
     print(out)
 
 

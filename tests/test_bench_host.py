@@ -61,16 +61,14 @@ def test_reference_arm_only_rank0_reports(monkeypatch):
 
 def test_ncu_traffic_entries_name_a_workload_a_kernel_and_a_capture():
     """Each DRAM-traffic figure the bench reports names a timed workload, a
-    kernel the bench times, and a committed capture summary that states the
-    same read and write bytes."""
+    kernel the bench times, the source hash it was taken of, and a committed
+    capture summary that states the same read and write bytes."""
     import re
     import graphgen
-    kernels = {"masked product, count", "masked product, support", "triangle lists",
-               "peel (k_peel)"}
-    assert bench.NCU_TRAFFIC
     for (workload, kernel), entry in bench.NCU_TRAFFIC.items():
         assert workload in graphgen.WORKLOADS
-        assert kernel in kernels
+        assert kernel in bench.KERNEL_SOURCE
+        assert len(entry["source_sha256"]) == 64
         path = re.search(r"profiles/\S+\.md", entry["source"]).group(0)
         text = open(os.path.join(ROOT, path)).read()
         gb = [float(x) for x in re.findall(r"(\d+\.\d+) GB", text)]
@@ -78,3 +76,24 @@ def test_ncu_traffic_entries_name_a_workload_a_kernel_and_a_capture():
         # to the reported bytes (to the summary's rounding)
         assert any(abs((a + b) * 1e9 - entry["bytes"]) < 0.02e9 * max(1.0, (a + b) / 10)
                    for a, b in zip(gb, gb[1:])), (workload, kernel)
+
+
+def test_ncu_traffic_is_dropped_once_the_kernel_source_changes(monkeypatch):
+    """Captured bytes describe one version of a kernel: with another source
+    hash the bench reports no traffic."""
+    kernel = "masked product, support"
+    cur = bench.kernel_source_sha(kernel)
+    monkeypatch.setitem(bench.NCU_TRAFFIC, ("rmat24", kernel),
+                        {"bytes": 1, "source": "x", "source_sha256": cur})
+    assert bench.ncu_traffic("rmat24", kernel)["bytes"] == 1
+    monkeypatch.setitem(bench.NCU_TRAFFIC, ("rmat24", kernel),
+                        {"bytes": 1, "source": "x", "source_sha256": "0" * 64})
+    assert bench.ncu_traffic("rmat24", kernel) is None
+    assert bench.ncu_traffic("rmat24", "peel (k_peel)") is None or \
+        ("rmat24", "peel (k_peel)") in bench.NCU_TRAFFIC
+
+
+def test_oracle_fixture_gives_the_whole_workload_time():
+    full = bench.oracle_fixture("rmat20")
+    assert full["edges"] == 15699719 and full["wall_s"] > 0
+    assert bench.oracle_fixture("no_such_workload") is None
