@@ -455,11 +455,13 @@ int tc_debug_peel_mode(int mode);
  * Test hook: which kernel tc_count / tc_edge_support (and the triangle-list
  * build of the peel) use.  0 = automatic (one thread per oriented edge
  * merging the two out-lists when the largest out-list has at most 16
- * entries; else one block per row with its out-list in a shared-memory hash
- * table when the largest out-list fits; else one warp per oriented edge),
- * 1 = the row kernel where the graph allows it, 2 = always one warp per
- * edge, 3 = always one thread per edge.  All give the same results.
- * Returns the previous mode.
+ * entries; else the column kernel when the largest out-list fits its
+ * shared-memory hash table; else one warp per oriented edge), 1 = the
+ * column kernel (N+(v) hashed, the in-neighbours' out-lists above v
+ * streamed against it) where the graph allows it, 2 = always one warp per
+ * edge, 3 = always one thread per edge, 4 = the row kernel (N+(u) hashed,
+ * its out-neighbours' out-lists streamed) where the graph allows it.  All
+ * give the same results.  Returns the previous mode.
  */
 int tc_debug_intersect_mode(int mode);
 

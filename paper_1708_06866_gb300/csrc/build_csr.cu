@@ -216,22 +216,29 @@ __global__ void k_upper(const uint64_t* __restrict__ keys, int64_t nnz, int bits
     }
 }
 
+// [0] = largest degree, [1] = largest out-list, [2] = rows of degree at
+// most LIGHT_DEG (rows ascend by degree, so these are the rows below that
+// count: the column kernel's light columns).
 __global__ void k_row_stats(const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
-                            int32_t n, unsigned long long* __restrict__ out /* [0]=maxdeg [1]=maxout */) {
+                            int32_t n, unsigned long long* __restrict__ out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    unsigned long long md = 0, mo = 0;
+    unsigned long long md = 0, mo = 0, nl = 0;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
-        md = max(md, (unsigned long long)(rowptr[r + 1] - rowptr[r]));
+        const int64_t d = rowptr[r + 1] - rowptr[r];
+        md = max(md, (unsigned long long)d);
         mo = max(mo, (unsigned long long)(rowptr[r + 1] - upper[r]));
+        nl += d <= LIGHT_DEG;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         md = max(md, __shfl_xor_sync(0xffffffffu, md, o));
         mo = max(mo, __shfl_xor_sync(0xffffffffu, mo, o));
+        nl += __shfl_xor_sync(0xffffffffu, nl, o);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicMax(&out[0], md);
         atomicMax(&out[1], mo);
+        atomicAdd(&out[2], nl);
     }
 }
 
@@ -413,14 +420,15 @@ int build_graph(Graph* g, const int32_t* src, const int32_t* dst, cudaStream_t s
             k_oshift<<<grid_for(n), 256, 0, s>>>(g->upper, obase, n, g->oshift);
             TC_LAUNCH_CHECK("k_oshift");
         }
-        TC_CUDA_TRY(cudaMemsetAsync(g->dev_scalars, 0, 2 * sizeof(unsigned long long), s));
+        TC_CUDA_TRY(cudaMemsetAsync(g->dev_scalars, 0, 3 * sizeof(unsigned long long), s));
         k_row_stats<<<grid_for(n), 256, 0, s>>>(g->rowptr, g->upper, n, g->dev_scalars);
         TC_LAUNCH_CHECK("k_row_stats");
-        unsigned long long st[2];
+        unsigned long long st[3];
         TC_CUDA_TRY(cudaMemcpyAsync(st, g->dev_scalars, sizeof(st), cudaMemcpyDeviceToHost, s));
         TC_CUDA_TRY(cudaStreamSynchronize(s));
         g->max_deg = (int32_t)st[0];
         g->max_out = (int32_t)st[1];
+        g->light_rows = (int32_t)st[2];
         TC_TRY(check_dev_err(g->dev_err, s));
     }
     return TC_OK;

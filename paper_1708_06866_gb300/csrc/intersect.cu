@@ -20,6 +20,10 @@
 // from the bottom through shared-memory cursors of that row, so those writes
 // stay within one block's lifetime; the rest (the edge is (v, w)) from the
 // top through one global cursor per edge.
+// The default kernel (k_cols) takes the same product by columns: one
+// column v of the mask at a time, N+(v) in the table, and for each
+// in-neighbour u the part of N+(u) above v streamed against it (fewer
+// entries read: see k_cols); k_rows stays as a selectable form.
 // Graphs whose largest out-list exceeds the table capacity use k_edges_warp
 // (one warp per oriented edge, binary search in global memory).
 #include <algorithm>
@@ -332,6 +336,305 @@ __global__ void __launch_bounds__(IX_THREADS) k_edges_warp(
     }
 }
 
+// ---- column kernel: the masked product organised by the middle vertex
+//
+// Every triangle u < v < w (rank order) has exactly one middle vertex v.
+// The column kernel takes each column v of the mask L (its in-neighbours u,
+// the entries [rowptr[v], upper[v]) of row v), puts N+(v) into a
+// shared-memory hash table and, for every in-neighbour u, streams the part
+// of N+(u) above v against it: (L L^T)(u, v) = |N+(u) ∩ N+(v)| and only
+// w > v can lie in N+(v).  Per oriented edge that reads |N+(u) above v|
+// entries instead of the row kernel's |N+(v)|; on R-MAT graphs the total is
+// 3-4x smaller (the sum over u of |N+(u)|^2 / 2 against the sum over edges
+// of |N+(v)|), because degree ordering makes the lower vertex's out-list the
+// short one.
+//
+// Columns of vertices of degree > LIGHT_DEG (the highest ranks) get one block
+// each, its warps sharing the in-neighbours; the rest (most of the vertices)
+// get one warp each with a warp-private table, so light columns pay no block
+// barrier.  In-neighbour u's segment of N+(u) starts after v's own entry,
+// at position eid(u, v) + oshift[u]; segments longer than CX_SHORT are
+// streamed by the whole warp (coalesced, CX_UNROLL chunks in flight),
+// shorter ones by one lane each.
+//
+// Credits of a triangle (u, v, w) found at N+(u) position p, table slot h:
+// (v, w) is the column's own edge (position pos[h] of N+(v)): a shared
+// counter, flushed once per column; (u, w) is edge p - oshift[u]: a global
+// atomic; (u, v): one add per segment.  LISTS writes the pair into the three
+// lists: (v, w) from the bottom through the column's shared cursors (its
+// bottom entries come only from this column), (u, v) and (u, w) from the top
+// through the global per-edge cursors.
+
+#ifndef TC_CX_SHORT
+#define TC_CX_SHORT 16    // in-neighbour segments up to this length: one lane each
+#endif
+#ifndef TC_CX_UNROLL
+#define TC_CX_UNROLL 4    // 32-wide chunks of a long segment in flight per warp pass
+#endif
+constexpr int CX_LIGHT_LOG_CAP = 8;  // warp table: 256 slots for <= LIGHT_DEG entries (load <= 1/4)
+constexpr int CX_LIGHT_CAP = 1 << CX_LIGHT_LOG_CAP;
+
+struct ColArgs {
+    const int64_t* rowptr;
+    const int64_t* upper;
+    const int32_t* col;
+    const int32_t* eid;
+    const int64_t* oshift;
+    int32_t n;
+    int32_t n_light;   // ranks [0, n_light) are light columns
+    int32_t* sup;
+    const unsigned long long* off;
+    unsigned int* top;
+    int2* pairs;
+    unsigned int* next;  // [0] heavy columns taken, [1] light columns taken
+    unsigned long long* partials;
+    int max_log_cap;
+    int max_pos;
+    int* err;
+};
+
+// One column's in-neighbours [i_first, i1) in steps of i_stride (32 per warp
+// of the group); returns the triangles found.  P: table position type.
+template <int MODE, typename P>
+__device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const int32_t* keys,
+                                                       const P* pos, int log_cap, int32_t* cnt,
+                                                       const unsigned int* sbase, int64_t ev,
+                                                       int32_t vmax, int64_t i_first, int64_t i1,
+                                                       int64_t i_stride) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long acc = 0;
+    for (int64_t ib = i_first; ib < i1; ib += i_stride) {
+        const int64_t i = ib + lane;
+        int64_t s = 0, end = 0, ou = 0;
+        int32_t e_uv = 0;
+        if (i < i1) {
+            const int32_t u = a.col[i];
+            e_uv = a.eid[i];
+            ou = a.oshift[u];
+            s = (int64_t)e_uv + ou + 1;  // N+(u) entries after v
+            end = a.rowptr[u + 1];
+        }
+        const int64_t len = end - s;
+        // a triangle (u, v, w) found at N+(u) position p, slot h
+        auto hit_support = [&](int h, int64_t p, int64_t o) {
+            atomicAdd(&cnt[pos[h]], 1);
+            atomicAdd(&a.sup[p - o], 1);
+        };
+        // long segments: the whole warp, one after another
+        unsigned lng = __ballot_sync(0xffffffffu, len > TC_CX_SHORT);
+        while (lng) {
+            const int src = __ffs(lng) - 1;
+            lng &= lng - 1;
+            const int64_t ss = __shfl_sync(0xffffffffu, s, src);
+            const int64_t se = __shfl_sync(0xffffffffu, end, src);
+            const int64_t so = __shfl_sync(0xffffffffu, ou, src);
+            const int32_t suv = __shfl_sync(0xffffffffu, e_uv, src);
+            uint32_t c = 0;
+            for (int64_t cb = ss; cb < se; cb += 32 * TC_CX_UNROLL) {
+                int32_t w[TC_CX_UNROLL];
+#pragma unroll
+                for (int q = 0; q < TC_CX_UNROLL; ++q) {
+                    const int64_t p = cb + 32 * q + lane;
+                    w[q] = p < se ? a.col[p] : INT_MAX;
+                }
+                // segments ascend: once a chunk starts above max N+(v), nothing later matches
+                if (__shfl_sync(0xffffffffu, w[0], 0) > vmax) break;
+                int h[TC_CX_UNROLL];
+#pragma unroll
+                for (int q = 0; q < TC_CX_UNROLL; ++q)
+                    h[q] = w[q] <= vmax ? table_find(keys, log_cap, w[q]) : -1;
+#pragma unroll
+                for (int q = 0; q < TC_CX_UNROLL; ++q) {
+                    const int64_t p = cb + 32 * q + lane;
+                    if (MODE == LISTS) {
+                        // the chunk's triangles share (u, v): one top append for all
+                        const unsigned msk = __ballot_sync(0xffffffffu, h[q] >= 0);
+                        if (msk) {
+                            const int ldr = __ffs(msk) - 1;
+                            unsigned base = 0;
+                            if (lane == ldr) base = atomicSub(&a.top[suv], (unsigned)__popc(msk));
+                            base = __shfl_sync(0xffffffffu, base, ldr) - (unsigned)__popc(msk);
+                            if (h[q] >= 0) {
+                                const int iw = pos[h[q]];
+                                const int32_t e_vw = (int32_t)(ev + iw), e_uw = (int32_t)(p - so);
+                                a.pairs[base + __popc(msk & lanemask_lt())] = make_int2(e_uw, e_vw);
+                                a.pairs[atomicSub(&a.top[e_uw], 1u) - 1u] = make_int2(suv, e_vw);
+                                a.pairs[sbase[iw] + atomicAdd((unsigned int*)&cnt[iw], 1u)] =
+                                    make_int2(suv, e_uw);
+                            }
+                        }
+                    }
+                    if (h[q] >= 0) {
+                        ++c;
+                        if (MODE == SUPPORT) hit_support(h[q], p, so);
+                    }
+                }
+            }
+            c = warp_sum(c);
+            if (lane == 0) {
+                acc += c;
+                if (MODE == SUPPORT && c) atomicAdd(&a.sup[suv], (int)c);
+            }
+        }
+        // short segments: one lane each, four entries in flight
+        if (len > 0 && len <= TC_CX_SHORT) {
+            uint32_t c = 0;
+            for (int64_t p = s; p < end; p += 4) {
+                int32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) w[q] = p + q < end ? a.col[p + q] : INT_MAX;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (w[q] > vmax) continue;
+                    const int h = table_find(keys, log_cap, w[q]);
+                    if (h < 0) continue;
+                    ++c;
+                    if (MODE == SUPPORT) hit_support(h, p + q, ou);
+                    if (MODE == LISTS) {
+                        const int iw = pos[h];
+                        const int32_t e_vw = (int32_t)(ev + iw), e_uw = (int32_t)(p + q - ou);
+                        a.pairs[atomicSub(&a.top[e_uv], 1u) - 1u] = make_int2(e_uw, e_vw);
+                        a.pairs[atomicSub(&a.top[e_uw], 1u) - 1u] = make_int2(e_uv, e_vw);
+                        a.pairs[sbase[iw] + atomicAdd((unsigned int*)&cnt[iw], 1u)] =
+                            make_int2(e_uv, e_uw);
+                    }
+                }
+                if (w[3] > vmax) break;
+            }
+            acc += c;
+            if (MODE == SUPPORT && c) atomicAdd(&a.sup[e_uv], (int)c);
+        }
+    }
+    return acc;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(RX_THREADS) k_cols(ColArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_col;
+    __shared__ unsigned long long s_acc[RX_WARPS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long acc = 0;
+    const int32_t n_heavy = a.n - a.n_light;
+
+    // heavy columns, highest rank first: one block each
+    {
+        const int max_cap = 1 << a.max_log_cap;
+        int32_t* keys = reinterpret_cast<int32_t*>(smem);
+        uint16_t* pos = reinterpret_cast<uint16_t*>(keys + max_cap);
+        int32_t* cnt = reinterpret_cast<int32_t*>(pos + max_cap);
+        unsigned int* sbase = reinterpret_cast<unsigned int*>(cnt + a.max_pos);
+        for (;;) {
+            if (threadIdx.x == 0) s_col = (int)atomicAdd(&a.next[0], 1u);
+            __syncthreads();
+            const int c = s_col;
+            __syncthreads();
+            if (c >= n_heavy) break;
+            const int32_t v = a.n - 1 - c;
+            const int64_t i0 = a.rowptr[v], b0 = a.upper[v], b1 = a.rowptr[v + 1];
+            const int dv = (int)(b1 - b0);
+            if (dv < 1 || b0 == i0) continue;  // no out-list or no in-neighbour: no triangle
+            const int64_t ev = b0 - (MODE == COUNT ? 0 : a.oshift[v]);
+            const int log_cap = min(table_log_cap(dv), a.max_log_cap);
+            const int cap = 1 << log_cap;
+            for (int i = threadIdx.x; i < cap; i += RX_THREADS) keys[i] = -1;
+            if (MODE != COUNT)
+                for (int i = threadIdx.x; i < dv; i += RX_THREADS) {
+                    cnt[i] = 0;
+                    if (MODE == LISTS) sbase[i] = (unsigned int)a.off[ev + i];
+                }
+            __syncthreads();
+            for (int i = threadIdx.x; i < dv; i += RX_THREADS) {
+                const int32_t w = a.col[b0 + i];
+                uint32_t h = slot_of(w, log_cap);
+                while (atomicCAS(&keys[h], -1, w) != -1) h = (h + 1) & (cap - 1);
+                pos[h] = (uint16_t)i;
+            }
+            __syncthreads();
+            const int32_t vmax = a.col[b1 - 1];
+            acc += col_walk<MODE>(a, keys, pos, log_cap, cnt, sbase, ev, vmax,
+                                  i0 + 32 * warp, b0, 32 * RX_WARPS);
+            __syncthreads();
+            if (MODE == SUPPORT)
+                for (int i = threadIdx.x; i < dv; i += RX_THREADS)
+                    if (cnt[i]) atomicAdd(&a.sup[ev + i], cnt[i]);
+            __syncthreads();
+        }
+    }
+
+    // light columns: one warp each, warp-private table; each warp takes 32
+    // columns at a time (one counter update per 32 columns)
+    {
+        constexpr int per_warp = CX_LIGHT_CAP * 4 + CX_LIGHT_CAP + LIGHT_DEG * 8;
+        unsigned char* base = smem + (size_t)warp * per_warp;
+        int32_t* keys = reinterpret_cast<int32_t*>(base);
+        uint8_t* pos = reinterpret_cast<uint8_t*>(keys + CX_LIGHT_CAP);
+        int32_t* cnt = reinterpret_cast<int32_t*>(pos + CX_LIGHT_CAP);
+        unsigned int* sbase = reinterpret_cast<unsigned int*>(cnt + LIGHT_DEG);
+        for (;;) {
+            unsigned c0 = 0;
+            if (lane == 0) c0 = atomicAdd(&a.next[1], 32u);
+            c0 = __shfl_sync(0xffffffffu, c0, 0);
+            if (c0 >= (unsigned)a.n_light) break;
+            const int cend = (int)min((unsigned)a.n_light, c0 + 32u);
+            for (int c = (int)c0; c < cend; ++c) {
+                const int32_t v = a.n_light - 1 - c;
+                const int64_t i0 = a.rowptr[v], b0 = a.upper[v], b1 = a.rowptr[v + 1];
+                const int dv = (int)(b1 - b0);
+                if (dv < 1 || b0 == i0) continue;
+                // the warp table is sized for LIGHT_DEG entries; a light
+                // column's out-list is at most its degree (never taken)
+                if (dv > LIGHT_DEG) {
+                    if (lane == 0) atomicOr(a.err, DEV_ERR_BOUNDS);
+                    continue;
+                }
+                const int64_t ev = b0 - (MODE == COUNT ? 0 : a.oshift[v]);
+                for (int i = lane; i < CX_LIGHT_CAP; i += 32) keys[i] = -1;
+                if (MODE != COUNT)
+                    for (int i = lane; i < dv; i += 32) {
+                        cnt[i] = 0;
+                        if (MODE == LISTS) sbase[i] = (unsigned int)a.off[ev + i];
+                    }
+                __syncwarp();
+                for (int i = lane; i < dv; i += 32) {
+                    const int32_t w = a.col[b0 + i];
+                    uint32_t h = slot_of(w, CX_LIGHT_LOG_CAP);
+                    while (atomicCAS(&keys[h], -1, w) != -1) h = (h + 1) & (CX_LIGHT_CAP - 1);
+                    pos[h] = (uint8_t)i;
+                }
+                __syncwarp();
+                const int32_t vmax = a.col[b1 - 1];
+                acc += col_walk<MODE>(a, keys, pos, CX_LIGHT_LOG_CAP, cnt, sbase, ev, vmax, i0, b0,
+                                      32);
+                __syncwarp();
+                if (MODE == SUPPORT)
+                    for (int i = lane; i < dv; i += 32)
+                        if (cnt[i]) atomicAdd(&a.sup[ev + i], cnt[i]);
+                __syncwarp();
+            }
+        }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) s_acc[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < RX_WARPS; ++w) t += s_acc[w];
+        a.partials[blockIdx.x] = t;
+    }
+}
+
+// Dynamic shared memory of the column kernel: the heavy columns' table and
+// per-position arrays (as the row kernel's), or the warps' light tables,
+// whichever is larger (the two phases reuse the same memory).
+size_t cols_smem(int log_cap, int mode, int max_pos) {
+    const size_t cap = (size_t)1 << log_cap;
+    const size_t per = mode == SUPPORT ? 4 : mode == LISTS ? 8 : 0;
+    const size_t heavy = cap * 4 + cap * 2 + per * (size_t)std::max(max_pos, 1) + 16;
+    const size_t light = (size_t)RX_WARPS * (CX_LIGHT_CAP * 4 + CX_LIGHT_CAP + LIGHT_DEG * 8);
+    return std::max(heavy, light);
+}
+
 // Sum of the per-block partial counts (one block, no atomics).
 __global__ void __launch_bounds__(1024) k_reduce_partials(const unsigned long long* __restrict__ p,
                                                           int64_t count,
@@ -513,6 +816,55 @@ int launch_rows(Graph* g, int32_t* sup, const unsigned long long* off, unsigned 
     return TC_OK;
 }
 
+int ensure_cols_smem_limit() {
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    TC_CUDA_TRY(cudaGetDevice(&dev));
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load() & bit) return TC_OK;
+    const int sm_max = (int)cols_smem(max_table_log_cap(RX_MAX_OUT), LISTS, RX_MAX_OUT);
+    TC_CUDA_TRY(cudaFuncSetAttribute(k_cols<COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_max));
+    TC_CUDA_TRY(cudaFuncSetAttribute(k_cols<SUPPORT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_max));
+    TC_CUDA_TRY(cudaFuncSetAttribute(k_cols<LISTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_max));
+    done.fetch_or(bit);
+    return TC_OK;
+}
+
+template <int MODE>
+int launch_cols(Graph* g, int32_t* sup, const unsigned long long* off, unsigned int* top,
+                int2* pairs, unsigned long long* partials, int blocks, cudaStream_t s) {
+    TC_TRY(ensure_cols_smem_limit());
+    if (g->max_out > RX_MAX_OUT) return fail(TC_EINVAL, "internal: column kernel above its table size");
+    const int lc = rows_log_cap(g);
+    const int max_pos = std::max(g->max_out, 1);
+    const size_t sm = cols_smem(lc, MODE, max_pos);
+    unsigned int* next = reinterpret_cast<unsigned int*>(g->dev_scalars + 5);
+    TC_CUDA_TRY(cudaMemsetAsync(next, 0, 2 * sizeof(unsigned int), s));
+    ColArgs a{g->rowptr, g->upper, g->col, g->eid, g->oshift, g->n, g->light_rows, sup, off, top,
+              pairs, next, partials, lc, max_pos, g->dev_err};
+    k_cols<MODE><<<blocks, RX_THREADS, sm, s>>>(a);
+    TC_LAUNCH_CHECK("k_cols");
+    return TC_OK;
+}
+
+int cols_blocks(Graph* g, int mode) {
+    int per_sm = 0;
+    const size_t sm = cols_smem(rows_log_cap(g), mode, std::max(g->max_out, 1));
+    cudaError_t e = cudaSuccess;
+    if (ensure_cols_smem_limit() != TC_OK) per_sm = 1;
+    else if (mode == COUNT)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cols<COUNT>, RX_THREADS, sm);
+    else if (mode == SUPPORT)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cols<SUPPORT>, RX_THREADS, sm);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cols<LISTS>, RX_THREADS, sm);
+    if (e != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return num_sms() * per_sm;
+}
+
 int rows_blocks(Graph* g, int mode) {
     int per_sm = 0;
     const size_t sm = rows_smem(rows_log_cap(g), mode, std::max(g->max_out, 1));
@@ -550,17 +902,23 @@ int graph_wedge_work(Graph* g, int64_t* out, cudaStream_t s) {
     return TC_OK;
 }
 
-// The intersection kernel a call uses: 1 = one block per row (hash table),
-// 2 = one warp per oriented edge, 3 = one thread per oriented edge.  form 0
-// (automatic, unless the test hook forces one): threads for small out-lists,
-// rows while the largest out-list fits the table, else warps.
+// The intersection kernel a call uses: 1 = by columns (k_cols: hash table
+// of N+(v), in-neighbours' segments streamed), 2 = one warp per oriented
+// edge, 3 = one thread per oriented edge, 4 = by rows (k_rows: hash table of
+// N+(u), out-neighbours' lists streamed).  form 0 (automatic, unless the
+// test hook forces one): threads for small out-lists, columns while the
+// largest out-list fits the table, else warps.
 int concrete_form(const Graph* g, int form) {
     const int f = form != 0 ? form : intersect_mode();
     if (f == 3) return 3;
     if (f == 2) return 2;
-    if (f == 1) return g->max_out <= RX_MAX_OUT ? 1 : 2;
+    if (f == 1 || f == 4) return g->max_out <= RX_MAX_OUT ? f : 2;
     if (g->max_out <= THREAD_MAX_OUT) return 3;
     return g->max_out <= RX_MAX_OUT ? 1 : 2;
+}
+
+int product_blocks(Graph* g, int f, int mode) {
+    return f == 1 ? cols_blocks(g, mode) : f == 4 ? rows_blocks(g, mode) : num_sms() * 8;
 }
 
 int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangles,
@@ -571,15 +929,18 @@ int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangle
         return TC_OK;
     }
     const int f = concrete_form(g, form);
-    const bool rows = f == 1;
-    const int blocks = rows ? rows_blocks(g, want_support ? SUPPORT : COUNT) : num_sms() * 8;
+    const int blocks = product_blocks(g, f, want_support ? SUPPORT : COUNT);
     Scratch sc(s);
     unsigned long long* partials;
     TC_TRY(sc.alloc(&partials, blocks));
     if (want_support) TC_CUDA_TRY(cudaMemsetAsync(sup, 0, sizeof(int32_t) * m, s));
     KernelTimer timer;
     TC_TRY(timer.start(s));
-    if (rows) {
+    if (f == 1) {
+        if (want_support)
+            TC_TRY(launch_cols<SUPPORT>(g, sup, nullptr, nullptr, nullptr, partials, blocks, s));
+        else TC_TRY(launch_cols<COUNT>(g, nullptr, nullptr, nullptr, nullptr, partials, blocks, s));
+    } else if (f == 4) {
         if (want_support)
             TC_TRY(launch_rows<SUPPORT>(g, sup, nullptr, nullptr, nullptr, partials, blocks, s));
         else TC_TRY(launch_rows<COUNT>(g, nullptr, nullptr, nullptr, nullptr, partials, blocks, s));
@@ -657,8 +1018,10 @@ int plan_triangle_lists(Graph* g, Scratch& sc, ListsPlan* lp) {
     lp->chunks = (m + SC_CHUNK - 1) / SC_CHUNK;
     TC_TRY(sc.alloc(&lp->sums, lp->chunks));
     TC_TRY(sc.alloc(&lp->top, m));
-    lp->thread = concrete_form(g, 0) == 3;
-    lp->blocks = lp->thread ? num_sms() * 8 : rows_blocks(g, LISTS);
+    lp->form = concrete_form(g, 0);
+    if (lp->form == 2) lp->form = 1;  // lists need a table kernel (the caller checked the size)
+    lp->thread = lp->form == 3;
+    lp->blocks = product_blocks(g, lp->form, LISTS);
     TC_TRY(sc.alloc(&lp->partials, lp->blocks));
     return TC_OK;
 }
@@ -685,8 +1048,10 @@ int enqueue_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off
             g->ends, g->rowptr, g->upper, g->col, g->oshift, m, nullptr, lp->top, pairs,
             lp->partials);
         TC_LAUNCH_CHECK("k_edges_thread");
-    } else {
+    } else if (lp->form == 4) {
         TC_TRY(launch_rows<LISTS>(g, nullptr, off, lp->top, pairs, lp->partials, lp->blocks, s));
+    } else {
+        TC_TRY(launch_cols<LISTS>(g, nullptr, off, lp->top, pairs, lp->partials, lp->blocks, s));
     }
     TC_TRY(lp->timer.stop(s));
     return TC_OK;

@@ -414,7 +414,7 @@ const char* tc_last_error(void) { return tc::t_last_error.c_str(); }
 int64_t tc_debug_fail_alloc(int64_t nth) { return tc::g_fail_alloc.exchange(nth < 0 ? 0 : nth); }
 
 int tc_debug_intersect_mode(int mode) {
-    if (mode < 0 || mode > 3) return tc::g_intersect_mode.load();
+    if (mode < 0 || mode > 4) return tc::g_intersect_mode.load();
     return tc::g_intersect_mode.exchange(mode);
 }
 

@@ -46,11 +46,16 @@ enum : int {
 
 int64_t spin_limit_ns();
 
+// Columns of the masked product whose vertex has at most this degree are
+// processed by one warp each (warp-private table); the others by one block.
+constexpr int LIGHT_DEG = 64;
+
 // Which form of the peel to use (test hook; PEEL_AUTO by default).
 enum : int { PEEL_AUTO = 0, PEEL_LISTS = 1, PEEL_INTERSECT = 2 };
 int peel_mode();
-// Which count/support kernel to use (test hook): 0 automatic, 1 row/hash
-// kernel where the graph allows it, 2 edge-per-warp binary search.
+// Which count/support kernel to use (test hook): 0 automatic, 1 column
+// kernel where the graph allows it, 2 edge-per-warp binary search, 3 thread
+// per edge, 4 row kernel where the graph allows it.
 int intersect_mode();
 
 // ---------------------------------------------------------------- memory
@@ -235,6 +240,7 @@ struct Graph {
     int64_t* oshift = nullptr;
     int32_t max_out = 0;      // max |N+(u)|
     int32_t max_deg = 0;
+    int32_t light_rows = 0;   // rows of degree <= LIGHT_DEG (the lowest ranks)
     int64_t wedge_work = -1;  // sum of |N+(u)| + |N+(v)| over oriented edges (lazy)
     int64_t last_peel_rounds = 0;  // bulk rounds of the most recent peel
     bool last_peel_lists = false;  // whether it used triangle lists
@@ -283,6 +289,7 @@ struct ListsPlan {
     int64_t chunks = 0;
     unsigned int* top = nullptr;         // per-edge fill positions from the list's end
     bool thread = false;                 // built by the thread-per-edge kernel
+    int form = 1;                        // the intersection kernel that builds them
     unsigned long long* partials = nullptr;
     int blocks = 0;
     KernelTimer timer;

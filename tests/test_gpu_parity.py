@@ -38,8 +38,9 @@ def gpu_all(src, dst, n, ks=(2, 3, 4, 5, 6)):
     """Every ABI call on one graph; the peel runs in both of its forms."""
     g = tc.tc_build_csr(dev(src), dev(dst), n)
     lo, hi = tc.tc_edges(g)
-    # the edge-per-warp kernel first, then the default (row kernel), whose
-    # supports the peel then reuses
+    # the edge-per-warp kernel first, the thread-per-edge and the row
+    # kernels, then the default (column kernel), whose supports the peel
+    # then reuses
     prev = tc.tc_debug_intersect_mode(2)
     try:
         T_warp = tc.tc_count(g)
@@ -49,13 +50,21 @@ def gpu_all(src, dst, n, ks=(2, 3, 4, 5, 6)):
         T_thread = tc.tc_count(g)
         s_thread, _ = tc.tc_edge_support(g)
         s_thread = s_thread.cpu().numpy()
+        tc.tc_debug_intersect_mode(4)   # the row kernel
+        T_rows = tc.tc_count(g)
+        s_rows, _ = tc.tc_edge_support(g)
+        s_rows = s_rows.cpu().numpy()
+        tc.tc_debug_intersect_mode(1)   # the column kernel (forced)
+        T_cols = tc.tc_count(g)
+        s_cols, _ = tc.tc_edge_support(g)
+        s_cols = s_cols.cpu().numpy()
     finally:
         tc.tc_debug_intersect_mode(prev)
     T = tc.tc_count(g)
     s, T2 = tc.tc_edge_support(g)
     out = dict(m=g.m, lo=lo.cpu().numpy(), hi=hi.cpu().numpy(), T=T, T2=T2,
                s=s.cpu().numpy(), peel={}, T_warp=T_warp, s_warp=s_warp, T_thread=T_thread,
-               s_thread=s_thread)
+               s_thread=s_thread, T_rows=T_rows, s_rows=s_rows, T_cols=T_cols, s_cols=s_cols)
     for name, mode in PEEL_MODES.items():
         prev = tc.tc_debug_peel_mode(mode)
         try:
@@ -87,6 +96,8 @@ def check(src, dst, n, ks=(2, 3, 4, 5, 6)):
     assert np.array_equal(got["s"], og.support())
     assert np.array_equal(got["s_warp"], got["s"])
     assert got["T_thread"] == T and np.array_equal(got["s_thread"], got["s"])
+    assert got["T_rows"] == T and np.array_equal(got["s_rows"], got["s"])
+    assert got["T_cols"] == T and np.array_equal(got["s_cols"], got["s"])
     kmax, truss = og.truss_decomposition()
     for name, res in got["peel"].items():
         for k in ks:
@@ -417,7 +428,7 @@ def test_every_intersection_kernel_builds_the_same_lists():
     src, dst, n = graphgen.rmat(12, 16, seed=5)
     og = oracle.OracleGraph.from_edges(src, dst, n)
     want_kmax, want_truss = og.truss_decomposition()
-    for imode in (1, 2, 3):
+    for imode in (1, 2, 3, 4):
         g = tc.tc_build_csr(dev(src), dev(dst), n)
         pi = tc.tc_debug_intersect_mode(imode)
         pp = tc.tc_debug_peel_mode(PEEL_MODES["lists"])
