@@ -259,6 +259,29 @@ def run_step(tc, torch, src, dst, n, wl, stream, ev=None, outs=None, infos=None)
     return m, T, res
 
 
+def product_bytes(info, n, T):
+    """Algorithmic bytes of the masked-product kernels (count, support,
+    triangle lists) for the kernel the library ran, plus the merge-operand
+    bytes of the row formulation (the same for every kernel).
+
+    Column kernel (product_form 1): every out-list entry it streams, 4 B per
+    entry of N+(u) above v (column_work entries); each out-list read once
+    into a table (4 B per edge); per in-neighbour entry its id, edge id and
+    the in-neighbour's row offset and edge shift (24 B per edge); per column
+    its row bounds and edge shift (24 B per vertex).  Other kernels: both
+    out-lists of every oriented edge (4 B per entry, wedge_work entries),
+    the row offsets (8 B per vertex) and the oriented edges' ids (4 B).
+    Support adds a 4-B write per edge; the list build the 8-B pair written
+    into each of the three lists of a triangle (24 B per triangle)."""
+    m = info["m"]
+    merge = 4 * info["wedge_work"] + 8 * (n + 1) + 4 * m
+    if info.get("product_form") == 1:
+        count = 4 * info["column_work"] + 28 * m + 24 * n
+    else:
+        count = merge
+    return count, count + 4 * m, count + 24 * T, merge
+
+
 def kernel_rooflines(infos, count_bytes, support_bytes, lists_bytes, peak):
     """Per main kernel: launches, mean device time, algorithmic bytes, GB/s."""
     acc = {}
@@ -460,19 +483,14 @@ def bench_ours(args, rank, world):
     flush = torch.empty(args.flush_mb << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
 
-    # graph sizes and the algorithmic bytes of the masked-product kernels:
-    # every list entry they merge (4 B), the row offsets (8 B per vertex),
-    # the edge ids of the oriented edges (4 B); support adds a 4-B write per
-    # edge; the triangle-list build adds the 8-B pair written per incidence
+    # graph sizes and the algorithmic bytes of the masked-product kernels
     g = tc.tc_build_csr(src, dst, n, stream=stream)
     wedge = tc.tc_graph_wedge_work(g, stream=stream)
     T0 = tc.tc_count(g, stream=stream)
     info = tc.tc_graph_info(g)
     g.free()
     m = info["m"]
-    count_bytes = 4 * wedge + 8 * (n + 1) + 4 * m
-    support_bytes = count_bytes + 4 * m
-    lists_bytes = count_bytes + 24 * T0
+    count_bytes, support_bytes, lists_bytes, merge_bytes = product_bytes(info, n, T0)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -529,6 +547,9 @@ def bench_ours(args, rank, world):
                       "m_in": info["m_in"], "m": m, "triangles": T,
                       "truss": res, "max_degree": info["max_degree"],
                       "max_out_degree": info["max_out"], "wedge_work": wedge,
+                      "column_work": info["column_work"],
+                      "product_form": {1: "columns", 2: "warp per edge", 3: "thread per edge",
+                                       4: "rows"}.get(info["product_form"]),
                       "l2": f"flushed between steps ({args.flush_mb} MB write)",
                       "parallelism": "replicas" if world > 1 else "single"},
            "phases_ms": {k: round(float(np.mean(v)), 3) for k, v in phases.items()},
@@ -536,6 +557,14 @@ def bench_ours(args, rank, world):
                           "(T = sum(s)/3); count: tc_count returns that T (no launch); "
                           "truss: triangle-list build (when the lists fit) + peel",
            "roofline": roofline, "kernels": kernels, "peel_work_per_launch": peel_work,
+           # the row formulation's merge operands (both out-lists of every
+           # oriented edge): the same for every kernel, so B / time is an
+           # effective rate that exceeds the peak when a kernel reads less
+           "support_merge_operand_bytes": {
+               "bytes": merge_bytes + 4 * m,
+               "effective_gbs": round((merge_bytes + 4 * m) / (kernels["masked product, support"]
+                                                                ["ms_per_launch"] * 1e6), 1)
+               if "masked product, support" in kernels else None},
            "gpu_launches": launches,
            "clocks": sampler.summary(),
            # the paper's other measures (Section IV): energy, memory, processor

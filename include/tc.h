@@ -170,7 +170,10 @@ typedef struct {
     int64_t peel_rounds;   /* bulk removal rounds of the most recent ktruss /
                               ktruss_max call on this graph (0 if none) */
     int64_t peel_lists;    /* 1 if that call read precomputed per-edge triangle
-                              lists, 0 if it intersected neighbour lists */
+                              lists, 0 if it intersected neighbour lists, 2 if
+                              it read lists kept only for the edges whose
+                              support was below a bound and intersected for
+                              the others */
     /* Device time (CUDA events on the call's stream, ns; -1 = not run or not
      * measured) of the latest launch on this graph of: the masked-product
      * kernel of tc_count, that of tc_edge_support (measured when the call
@@ -193,6 +196,13 @@ typedef struct {
     int64_t truss_cached;  /* 1 if the graph keeps the truss decomposition of
                               its latest ktruss_max (later ktruss calls then
                               threshold it instead of peeling) */
+    int64_t column_work;   /* sum over vertices u of |N+(u)| (|N+(u)| - 1) / 2:
+                              the out-list entries the column kernel streams
+                              (for each oriented edge (u, v), the entries of
+                              N+(u) above v), or -1 until tc_graph_wedge_work ran */
+    int64_t product_form;  /* the masked-product kernel of the latest tc_count /
+                              tc_edge_support launch: 1 columns, 2 warp per
+                              edge, 3 thread per edge, 4 rows; 0 if none */
 } tc_graph_info_t;
 
 /* Fills *info (host pointer) from values the library already holds; launches
@@ -200,7 +210,8 @@ typedef struct {
 int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream);
 
 /* Computes (once per graph, one kernel) the sum over oriented edges (u, v)
- * of |N+(u)| + |N+(v)| into *out (host).  Synchronises the stream. */
+ * of |N+(u)| + |N+(v)| into *out (host), and with it tc_graph_info's
+ * column_work.  Synchronises the stream. */
 int tc_graph_wedge_work(tc_graph* g, int64_t* out, void* cuda_stream);
 
 /*
@@ -444,10 +455,13 @@ int64_t tc_debug_fail_alloc(int64_t nth);
 
 /*
  * Test hook: which form of the peel ktruss / ktruss_max use.  0 = automatic
- * (per-edge triangle lists when they fit in free device memory, else
- * intersections of live neighbour lists), 1 = always triangle lists (where
- * the graph allows them), 2 = always intersections.  Both forms give the
- * same results.  Returns the previous mode; other values leave it unchanged.
+ * (per-edge triangle lists for every edge when they fit in free device
+ * memory, else lists for only the edges whose support is below 8 with
+ * intersections of live neighbour lists for the others when those fit, else
+ * intersections alone), 1 = triangle lists (for every edge where 3T < 2^32,
+ * else the bounded lists), 2 = always intersections, 3 = always the bounded
+ * lists with intersections.  All forms give the same results.  Returns the
+ * previous mode; other values leave it unchanged.
  */
 int tc_debug_peel_mode(int mode);
 

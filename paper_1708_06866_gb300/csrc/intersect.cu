@@ -81,13 +81,19 @@ __device__ __forceinline__ int table_find(const int32_t* keys, int log_cap, int3
     return (int)h;
 }
 
+// LISTS with bound > 0 writes only the lists of edges whose support (sup,
+// read-only in that mode) is below bound.
+__device__ __forceinline__ bool gets_list(const int32_t* sup, int32_t bound, int32_t e) {
+    return bound == 0 || sup[e] < bound;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(RX_THREADS) k_rows(
     const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
     const int32_t* __restrict__ col, const int64_t* __restrict__ oshift, int32_t n,
     int32_t* __restrict__ sup, const unsigned long long* __restrict__ off,
     unsigned int* __restrict__ top, int2* __restrict__ pairs, unsigned int* __restrict__ next_row,
-    unsigned long long* __restrict__ partials, int max_log_cap, int max_pos) {
+    unsigned long long* __restrict__ partials, int max_log_cap, int max_pos, int32_t bound) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int max_cap = 1 << max_log_cap;
     int32_t* keys = reinterpret_cast<int32_t*>(smem);
@@ -127,7 +133,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
                 const int32_t e = (int32_t)(eu + i);
                 cnt[i] = 0;
                 seid[i] = e;
-                sbase[i] = (unsigned int)off[e];
+                sbase[i] = gets_list(sup, bound, e) ? (unsigned int)off[e] : 0xffffffffu;
             }
         __syncthreads();
         for (int i = threadIdx.x; i < du; i += RX_THREADS) {
@@ -144,7 +150,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
             const int64_t b0 = upper[v], b1 = rowptr[v + 1];
             const int64_t ov = MODE == COUNT ? 0 : oshift[v];
             const int32_t e_uv = MODE == COUNT ? 0 : (int32_t)(eu + j);
-            const unsigned int base_uv = MODE == LISTS ? sbase[j] : 0u;
+            const unsigned int base_uv = MODE == LISTS ? sbase[j] : 0u;  // ~0u: no list
             uint32_t c = 0;
             // one hit: credit the triangle (u, v, w) found at N+(v) position p,
             // table slot h
@@ -163,15 +169,19 @@ __global__ void __launch_bounds__(RX_THREADS) k_rows(
                 if (!msk) return;
                 const int ldr = __ffs(msk) - 1;
                 unsigned base = 0;
-                if (lane == ldr) base = atomicAdd((unsigned int*)&cnt[j], (unsigned)__popc(msk));
+                if (lane == ldr && base_uv != 0xffffffffu)
+                    base = atomicAdd((unsigned int*)&cnt[j], (unsigned)__popc(msk));
                 base = __shfl_sync(0xffffffffu, base, ldr);
                 if (h >= 0) {
                     const int iw = pos[h];
                     const int32_t e_uw = seid[iw], e_vw = (int32_t)(p - ov);
-                    pairs[base_uv + base + __popc(msk & lanemask_lt())] = make_int2(e_uw, e_vw);
-                    pairs[sbase[iw] + atomicAdd((unsigned int*)&cnt[iw], 1u)] =
-                        make_int2(e_uv, e_vw);
-                    pairs[atomicSub(&top[e_vw], 1u) - 1u] = make_int2(e_uv, e_uw);
+                    if (base_uv != 0xffffffffu)
+                        pairs[base_uv + base + __popc(msk & lanemask_lt())] = make_int2(e_uw, e_vw);
+                    if (sbase[iw] != 0xffffffffu)
+                        pairs[sbase[iw] + atomicAdd((unsigned int*)&cnt[iw], 1u)] =
+                            make_int2(e_uv, e_vw);
+                    if (gets_list(sup, bound, e_vw))
+                        pairs[atomicSub(&top[e_vw], 1u) - 1u] = make_int2(e_uv, e_uw);
                 }
             };
             // TC_RX_UNROLL 32-wide chunks per pass: their loads are in flight
@@ -228,7 +238,7 @@ __global__ void __launch_bounds__(IX_THREADS) k_edges_thread(
     const int64_t* __restrict__ upper, const int32_t* __restrict__ col,
     const int64_t* __restrict__ oshift, int64_t m, int32_t* __restrict__ sup,
     unsigned int* __restrict__ top, int2* __restrict__ pairs,
-    unsigned long long* __restrict__ partials) {
+    unsigned long long* __restrict__ partials, int32_t bound) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long acc = 0;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
@@ -253,9 +263,12 @@ __global__ void __launch_bounds__(IX_THREADS) k_edges_thread(
                 if (MODE == LISTS) {
                     const int32_t e_uw = (int32_t)(a - ou), e_vw = (int32_t)(b - ov);
                     const int32_t e_uv = (int32_t)j;
-                    pairs[atomicSub(&top[e_uv], 1u) - 1u] = make_int2(e_uw, e_vw);
-                    pairs[atomicSub(&top[e_uw], 1u) - 1u] = make_int2(e_uv, e_vw);
-                    pairs[atomicSub(&top[e_vw], 1u) - 1u] = make_int2(e_uv, e_uw);
+                    if (gets_list(sup, bound, e_uv))
+                        pairs[atomicSub(&top[e_uv], 1u) - 1u] = make_int2(e_uw, e_vw);
+                    if (gets_list(sup, bound, e_uw))
+                        pairs[atomicSub(&top[e_uw], 1u) - 1u] = make_int2(e_uv, e_vw);
+                    if (gets_list(sup, bound, e_vw))
+                        pairs[atomicSub(&top[e_vw], 1u) - 1u] = make_int2(e_uv, e_uw);
                 }
                 ++a;
                 ++b;
@@ -364,6 +377,12 @@ __global__ void __launch_bounds__(IX_THREADS) k_edges_warp(
 // lists: (v, w) from the bottom through the column's shared cursors (its
 // bottom entries come only from this column), (u, v) and (u, w) from the top
 // through the global per-edge cursors.
+//
+// Lists for only the edges of support below a bound (LISTS, bound > 0): a
+// triangle needs an entry only if one of its edges has a list.  A segment
+// is streamed in full only when (u, v) has a list or some edge (v, w) of the
+// column does; otherwise only u's low out-entries above v (a compacted list
+// per row, lowptr / lowlist) are probed, each hit filling the (u, w) list.
 
 #ifndef TC_CX_SHORT
 #define TC_CX_SHORT 16    // in-neighbour segments up to this length: one lane each
@@ -371,7 +390,14 @@ __global__ void __launch_bounds__(IX_THREADS) k_edges_warp(
 #ifndef TC_CX_UNROLL
 #define TC_CX_UNROLL 4    // 32-wide chunks of a long segment in flight per warp pass
 #endif
-constexpr int CX_LIGHT_LOG_CAP = 8;  // warp table: 256 slots for <= LIGHT_DEG entries (load <= 1/4)
+#ifndef TC_CX_MIN_BLOCKS
+#define TC_CX_MIN_BLOCKS 7  // resident blocks per SM the register allocation must allow (latency-bound: occupancy pays)
+#endif
+#ifndef TC_CX_DYNAMIC
+#define TC_CX_DYNAMIC 1     // heavy columns: in-neighbour batches handed out dynamically
+#endif
+// warp table: 4 slots per entry for <= LIGHT_DEG entries (load <= 1/4)
+constexpr int CX_LIGHT_LOG_CAP = LIGHT_DEG <= 64 ? 8 : LIGHT_DEG <= 128 ? 9 : 10;
 constexpr int CX_LIGHT_CAP = 1 << CX_LIGHT_LOG_CAP;
 
 struct ColArgs {
@@ -391,7 +417,15 @@ struct ColArgs {
     int max_log_cap;
     int max_pos;
     int* err;
+    int32_t bound;                 // LISTS: lists only for supports below it (0: all)
+    const unsigned int* lowbits;   // ... one bit per edge: it gets a list
+    const unsigned int* lowpos;    // ... low edges with a smaller id (m + 1 entries)
+    const int2* lowlist;           // ... {w, edge id} of every low edge, in edge-id order
 };
+
+__device__ __forceinline__ bool low_bit(const unsigned int* bits, int32_t e) {
+    return (bits[e >> 5] >> (e & 31)) & 1u;
+}
 
 // One column's in-neighbours [i_first, i1) in steps of i_stride (32 per warp
 // of the group); returns the triangles found.  P: table position type.
@@ -399,22 +433,39 @@ template <int MODE, typename P>
 __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const int32_t* keys,
                                                        const P* pos, int log_cap, int32_t* cnt,
                                                        const unsigned int* sbase, int64_t ev,
-                                                       int32_t vmax, int64_t i_first, int64_t i1,
-                                                       int64_t i_stride) {
+                                                       int32_t vmax, bool col_low, int64_t i0,
+                                                       int64_t i1, unsigned int* next,
+                                                       int64_t stride = 32) {
     const int lane = threadIdx.x & 31;
+    const bool partial = MODE == LISTS && a.bound > 0;
     unsigned long long acc = 0;
-    for (int64_t ib = i_first; ib < i1; ib += i_stride) {
+    // batches of 32 in-neighbours: handed out by the shared counter (a
+    // block's warps sharing a column take them as they finish), or all to
+    // this warp
+    auto take = [&](int64_t done) -> int64_t {
+        if (!next) return done;  // static: i0, i0 + stride, ...
+        unsigned b = 0;
+        if (lane == 0) b = atomicAdd(next, 32u);
+        return i0 + (int64_t)__shfl_sync(0xffffffffu, b, 0);
+    };
+    for (int64_t ib = take(i0); ib < i1; ib = take(ib + stride)) {
         const int64_t i = ib + lane;
         int64_t s = 0, end = 0, ou = 0;
-        int32_t e_uv = 0;
+        int32_t e_uv = 0, u = 0;
+        bool luv = true;   // (u, v) has a list
+        bool full = true;  // the whole segment is streamed
         if (i < i1) {
-            const int32_t u = a.col[i];
+            u = a.col[i];
             e_uv = a.eid[i];
             ou = a.oshift[u];
             s = (int64_t)e_uv + ou + 1;  // N+(u) entries after v
             end = a.rowptr[u + 1];
+            if (partial) {
+                luv = low_bit(a.lowbits, e_uv);
+                full = luv || col_low;
+            }
         }
-        const int64_t len = end - s;
+        const int64_t len = full ? end - s : 0;
         // a triangle (u, v, w) found at N+(u) position p, slot h
         auto hit_support = [&](int h, int64_t p, int64_t o) {
             atomicAdd(&cnt[pos[h]], 1);
@@ -429,6 +480,7 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
             const int64_t se = __shfl_sync(0xffffffffu, end, src);
             const int64_t so = __shfl_sync(0xffffffffu, ou, src);
             const int32_t suv = __shfl_sync(0xffffffffu, e_uv, src);
+            const bool sluv = __shfl_sync(0xffffffffu, luv, src);
             uint32_t c = 0;
             for (int64_t cb = ss; cb < se; cb += 32 * TC_CX_UNROLL) {
                 int32_t w[TC_CX_UNROLL];
@@ -452,15 +504,20 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
                         if (msk) {
                             const int ldr = __ffs(msk) - 1;
                             unsigned base = 0;
-                            if (lane == ldr) base = atomicSub(&a.top[suv], (unsigned)__popc(msk));
+                            if (lane == ldr && sluv)
+                                base = atomicSub(&a.top[suv], (unsigned)__popc(msk));
                             base = __shfl_sync(0xffffffffu, base, ldr) - (unsigned)__popc(msk);
                             if (h[q] >= 0) {
                                 const int iw = pos[h[q]];
                                 const int32_t e_vw = (int32_t)(ev + iw), e_uw = (int32_t)(p - so);
-                                a.pairs[base + __popc(msk & lanemask_lt())] = make_int2(e_uw, e_vw);
-                                a.pairs[atomicSub(&a.top[e_uw], 1u) - 1u] = make_int2(suv, e_vw);
-                                a.pairs[sbase[iw] + atomicAdd((unsigned int*)&cnt[iw], 1u)] =
-                                    make_int2(suv, e_uw);
+                                if (sluv)
+                                    a.pairs[base + __popc(msk & lanemask_lt())] =
+                                        make_int2(e_uw, e_vw);
+                                if (!partial || low_bit(a.lowbits, e_uw))
+                                    a.pairs[atomicSub(&a.top[e_uw], 1u) - 1u] = make_int2(suv, e_vw);
+                                if (sbase[iw] != 0xffffffffu)
+                                    a.pairs[sbase[iw] + atomicAdd((unsigned int*)&cnt[iw], 1u)] =
+                                        make_int2(suv, e_uw);
                             }
                         }
                     }
@@ -493,10 +550,12 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
                     if (MODE == LISTS) {
                         const int iw = pos[h];
                         const int32_t e_vw = (int32_t)(ev + iw), e_uw = (int32_t)(p + q - ou);
-                        a.pairs[atomicSub(&a.top[e_uv], 1u) - 1u] = make_int2(e_uw, e_vw);
-                        a.pairs[atomicSub(&a.top[e_uw], 1u) - 1u] = make_int2(e_uv, e_vw);
-                        a.pairs[sbase[iw] + atomicAdd((unsigned int*)&cnt[iw], 1u)] =
-                            make_int2(e_uv, e_uw);
+                        if (luv) a.pairs[atomicSub(&a.top[e_uv], 1u) - 1u] = make_int2(e_uw, e_vw);
+                        if (!partial || low_bit(a.lowbits, e_uw))
+                            a.pairs[atomicSub(&a.top[e_uw], 1u) - 1u] = make_int2(e_uv, e_vw);
+                        if (sbase[iw] != 0xffffffffu)
+                            a.pairs[sbase[iw] + atomicAdd((unsigned int*)&cnt[iw], 1u)] =
+                                make_int2(e_uv, e_uw);
                     }
                 }
                 if (w[3] > vmax) break;
@@ -504,14 +563,29 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
             acc += c;
             if (MODE == SUPPORT && c) atomicAdd(&a.sup[e_uv], (int)c);
         }
+        // lists below a bound, segment not streamed: only u's low out-entries
+        // above v can close a triangle that needs an entry, in the (u, w) list
+        if (partial && i < i1 && !full && s < end) {
+            // u's low out-entries after v: edge ids e_uv + 1 .. (end - ou) - 1
+            const unsigned int l1 = a.lowpos[end - ou];
+            for (unsigned int q = a.lowpos[e_uv + 1]; q < l1; ++q) {
+                const int2 we = a.lowlist[q];  // {w, edge id of (u, w)}
+                if (we.x > vmax) break;
+                const int h = table_find(keys, log_cap, we.x);
+                if (h < 0) continue;
+                const int32_t e_vw = (int32_t)(ev + pos[h]);
+                a.pairs[atomicSub(&a.top[we.y], 1u) - 1u] = make_int2(e_uv, e_vw);
+            }
+        }
     }
     return acc;
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(RX_THREADS) k_cols(ColArgs a) {
+__global__ void __launch_bounds__(RX_THREADS, TC_CX_MIN_BLOCKS) k_cols(ColArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_col;
+    __shared__ unsigned int s_next;  // heavy column: next in-neighbour batch (offset)
     __shared__ unsigned long long s_acc[RX_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long acc = 0;
@@ -525,7 +599,10 @@ __global__ void __launch_bounds__(RX_THREADS) k_cols(ColArgs a) {
         int32_t* cnt = reinterpret_cast<int32_t*>(pos + max_cap);
         unsigned int* sbase = reinterpret_cast<unsigned int*>(cnt + a.max_pos);
         for (;;) {
-            if (threadIdx.x == 0) s_col = (int)atomicAdd(&a.next[0], 1u);
+            if (threadIdx.x == 0) {
+                s_col = (int)atomicAdd(&a.next[0], 1u);
+                s_next = 0;
+            }
             __syncthreads();
             const int c = s_col;
             __syncthreads();
@@ -538,12 +615,17 @@ __global__ void __launch_bounds__(RX_THREADS) k_cols(ColArgs a) {
             const int log_cap = min(table_log_cap(dv), a.max_log_cap);
             const int cap = 1 << log_cap;
             for (int i = threadIdx.x; i < cap; i += RX_THREADS) keys[i] = -1;
+            bool low = false;  // some edge (v, w) of the column has a list
             if (MODE != COUNT)
                 for (int i = threadIdx.x; i < dv; i += RX_THREADS) {
                     cnt[i] = 0;
-                    if (MODE == LISTS) sbase[i] = (unsigned int)a.off[ev + i];
+                    if (MODE == LISTS) {
+                        const bool has = a.bound == 0 || low_bit(a.lowbits, (int32_t)(ev + i));
+                        sbase[i] = has ? (unsigned int)a.off[ev + i] : 0xffffffffu;
+                        low |= has && a.bound > 0;
+                    }
                 }
-            __syncthreads();
+            const bool col_low = __syncthreads_or(low) != 0;
             for (int i = threadIdx.x; i < dv; i += RX_THREADS) {
                 const int32_t w = a.col[b0 + i];
                 uint32_t h = slot_of(w, log_cap);
@@ -552,8 +634,12 @@ __global__ void __launch_bounds__(RX_THREADS) k_cols(ColArgs a) {
             }
             __syncthreads();
             const int32_t vmax = a.col[b1 - 1];
-            acc += col_walk<MODE>(a, keys, pos, log_cap, cnt, sbase, ev, vmax,
-                                  i0 + 32 * warp, b0, 32 * RX_WARPS);
+            if (TC_CX_DYNAMIC)
+                acc += col_walk<MODE>(a, keys, pos, log_cap, cnt, sbase, ev, vmax, col_low, i0, b0,
+                                      &s_next);
+            else
+                acc += col_walk<MODE>(a, keys, pos, log_cap, cnt, sbase, ev, vmax, col_low,
+                                      i0 + 32 * warp, b0, nullptr, 32 * RX_WARPS);
             __syncthreads();
             if (MODE == SUPPORT)
                 for (int i = threadIdx.x; i < dv; i += RX_THREADS)
@@ -590,11 +676,17 @@ __global__ void __launch_bounds__(RX_THREADS) k_cols(ColArgs a) {
                 }
                 const int64_t ev = b0 - (MODE == COUNT ? 0 : a.oshift[v]);
                 for (int i = lane; i < CX_LIGHT_CAP; i += 32) keys[i] = -1;
+                bool low = false;
                 if (MODE != COUNT)
                     for (int i = lane; i < dv; i += 32) {
                         cnt[i] = 0;
-                        if (MODE == LISTS) sbase[i] = (unsigned int)a.off[ev + i];
+                        if (MODE == LISTS) {
+                            const bool has = a.bound == 0 || low_bit(a.lowbits, (int32_t)(ev + i));
+                            sbase[i] = has ? (unsigned int)a.off[ev + i] : 0xffffffffu;
+                            low |= has && a.bound > 0;
+                        }
                     }
+                const bool col_low = __any_sync(0xffffffffu, low);
                 __syncwarp();
                 for (int i = lane; i < dv; i += 32) {
                     const int32_t w = a.col[b0 + i];
@@ -604,8 +696,8 @@ __global__ void __launch_bounds__(RX_THREADS) k_cols(ColArgs a) {
                 }
                 __syncwarp();
                 const int32_t vmax = a.col[b1 - 1];
-                acc += col_walk<MODE>(a, keys, pos, CX_LIGHT_LOG_CAP, cnt, sbase, ev, vmax, i0, b0,
-                                      32);
+                acc += col_walk<MODE>(a, keys, pos, CX_LIGHT_LOG_CAP, cnt, sbase, ev, vmax, col_low,
+                                      i0, b0, nullptr, 32);
                 __syncwarp();
                 if (MODE == SUPPORT)
                     for (int i = lane; i < dv; i += 32)
@@ -652,18 +744,28 @@ __global__ void __launch_bounds__(1024) k_reduce_partials(const unsigned long lo
     }
 }
 
+// out[0] = sum over oriented edges of |N+(u)| + |N+(v)|; out[1] = sum over
+// rows u of |N+(u)| (|N+(u)| - 1) / 2.
 __global__ void k_wedge_work(const int2* __restrict__ ends,
                              const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
-                             int64_t m, unsigned long long* __restrict__ out) {
+                             int64_t m, int32_t n, unsigned long long* __restrict__ out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    unsigned long long acc = 0;
+    unsigned long long acc = 0, cw = 0;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
         const int2 uv = ends[j];
         acc += (unsigned long long)(rowptr[uv.x + 1] - upper[uv.x]) +
                (unsigned long long)(rowptr[uv.y + 1] - upper[uv.y]);
     }
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        const unsigned long long d = (unsigned long long)(rowptr[r + 1] - upper[r]);
+        cw += d * (d - (d > 0)) / 2;
+    }
     acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+    cw = warp_sum(cw);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[0], acc);
+        atomicAdd(&out[1], cw);
+    }
 }
 
 // ---- 64-bit exclusive scan of int32 values (offsets of the triangle lists)
@@ -687,14 +789,20 @@ __device__ unsigned long long block_sum64(unsigned long long v, unsigned long lo
     return t;
 }
 
+// Values at or above `bound` (when bound > 0) count as 0: the offsets of
+// lists kept only for the edges whose support is below it.
+__device__ __forceinline__ unsigned long long bounded(int32_t x, int32_t bound) {
+    return (bound > 0 && x >= bound) ? 0ull : (unsigned long long)x;
+}
+
 __global__ void __launch_bounds__(SC_THREADS) k_chunk_sums(const int32_t* __restrict__ x,
-                                                           int64_t n,
+                                                           int64_t n, int32_t bound,
                                                            unsigned long long* __restrict__ sums) {
     __shared__ unsigned long long sh[33];
     const int64_t base = (int64_t)blockIdx.x * SC_CHUNK;
     unsigned long long v = 0;
     for (int i = threadIdx.x; i < SC_CHUNK; i += SC_THREADS)
-        if (base + i < n) v += (unsigned long long)x[base + i];
+        if (base + i < n) v += bounded(x[base + i], bound);
     const unsigned long long t = block_sum64(v, sh);
     if (threadIdx.x == 0) sums[blockIdx.x] = t;
 }
@@ -725,6 +833,7 @@ __global__ void __launch_bounds__(1024) k_scan_sums64(unsigned long long* __rest
 
 // off[i] = sum of x[0..i); off[n] = total.
 __global__ void __launch_bounds__(SC_THREADS) k_chunk_scan(const int32_t* __restrict__ x, int64_t n,
+                                                           int32_t bound,
                                                            const unsigned long long* __restrict__ sums,
                                                            unsigned long long* __restrict__ off) {
     __shared__ unsigned long long sh[SC_THREADS];
@@ -735,7 +844,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_chunk_scan(const int32_t* __rest
 #pragma unroll
     for (int k = 0; k < SC_ITEMS; ++k) {
         const int64_t i = base + (int64_t)threadIdx.x * SC_ITEMS + k;
-        loc[k] = i < n ? (unsigned long long)x[i] : 0ull;
+        loc[k] = i < n ? bounded(x[i], bound) : 0ull;
         tsum += loc[k];
     }
     sh[threadIdx.x] = tsum;
@@ -761,6 +870,88 @@ __global__ void k_u32_from_u64(const unsigned long long* __restrict__ in, int64_
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
         out[i] = (unsigned int)in[i];
+}
+
+// Sum of the supports in (0, bound) and the number of such edges.
+__global__ void k_low_sums(const int32_t* __restrict__ sup, int64_t m, int32_t bound,
+                           unsigned long long* __restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long e = 0, c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const int32_t x = sup[i];
+        const bool low = x > 0 && x < bound;
+        e += low ? (unsigned long long)x : 0ull;
+        c += low;
+    }
+    e = warp_sum(e);
+    c = warp_sum(c);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[0], e);
+        atomicAdd(&out[1], c);
+    }
+}
+
+// Edges with a support in (0, bound) ("low": the edges that get lists):
+// lowbits holds one bit per edge; lowpos[e] counts the low edges with id
+// below e (m + 1 entries, an exclusive scan); lowlist[lowpos[e]] = {head
+// w of e, e} for every low e.  Edge ids follow the out-lists, so the low
+// out-entries of u after its out-neighbour v (edge e_uv) are lowlist
+// [lowpos[e_uv + 1], lowpos[end of u's out-edges]).
+__device__ __forceinline__ bool is_low(int32_t x, int32_t bound) { return x > 0 && x < bound; }
+
+__global__ void __launch_bounds__(SC_THREADS) k_low_chunk_counts(const int32_t* __restrict__ sup,
+                                                                 int64_t m, int32_t bound,
+                                                                 unsigned int* __restrict__ lowbits,
+                                                                 unsigned long long* __restrict__ sums) {
+    __shared__ unsigned long long sh[33];
+    const int64_t base = (int64_t)blockIdx.x * SC_CHUNK;
+    unsigned long long c = 0;
+    for (int i = threadIdx.x; i < SC_CHUNK; i += SC_THREADS) {
+        const int64_t e = base + i;
+        const bool low = e < m && is_low(sup[e], bound);
+        const unsigned bits = __ballot_sync(0xffffffffu, low);
+        if ((threadIdx.x & 31) == 0 && e < m) lowbits[e >> 5] = bits;
+        c += low;
+    }
+    const unsigned long long t = block_sum64(c, sh);
+    if (threadIdx.x == 0) sums[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_low_scan(const int32_t* __restrict__ sup,
+                                                         const int2* __restrict__ ends, int64_t m,
+                                                         int32_t bound,
+                                                         const unsigned long long* __restrict__ sums,
+                                                         unsigned int* __restrict__ lowpos,
+                                                         int2* __restrict__ lowlist) {
+    __shared__ unsigned int sh[SC_THREADS];
+    const int64_t base = (int64_t)blockIdx.x * SC_CHUNK;
+    bool low[SC_ITEMS];
+    unsigned int tsum = 0;
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k) {
+        const int64_t e = base + (int64_t)threadIdx.x * SC_ITEMS + k;
+        low[k] = e < m && is_low(sup[e], bound);
+        tsum += low[k];
+    }
+    sh[threadIdx.x] = tsum;
+    __syncthreads();
+    for (int o = 1; o < SC_THREADS; o <<= 1) {
+        const unsigned int y = threadIdx.x >= o ? sh[threadIdx.x - o] : 0u;
+        __syncthreads();
+        sh[threadIdx.x] += y;
+        __syncthreads();
+    }
+    unsigned int run = (unsigned int)sums[blockIdx.x] + sh[threadIdx.x] - tsum;
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k) {
+        const int64_t e = base + (int64_t)threadIdx.x * SC_ITEMS + k;
+        if (e < m) {
+            lowpos[e] = run;
+            if (low[k]) lowlist[run] = make_int2(ends[e].y, (int32_t)e);
+        }
+        if (e == m - 1) lowpos[m] = run + low[k];
+        run += low[k];
+    }
 }
 
 // The block's table must hold the largest table any row up to max_out
@@ -801,7 +992,8 @@ int ensure_rows_smem_limit() {
 
 template <int MODE>
 int launch_rows(Graph* g, int32_t* sup, const unsigned long long* off, unsigned int* top,
-                int2* pairs, unsigned long long* partials, int blocks, cudaStream_t s) {
+                int2* pairs, unsigned long long* partials, int blocks, cudaStream_t s,
+                int32_t bound = 0) {
     TC_TRY(ensure_rows_smem_limit());
     if (g->max_out > RX_MAX_OUT) return fail(TC_EINVAL, "internal: row kernel above its table size");
     const int lc = rows_log_cap(g);
@@ -811,7 +1003,7 @@ int launch_rows(Graph* g, int32_t* sup, const unsigned long long* off, unsigned 
     TC_CUDA_TRY(cudaMemsetAsync(next_row, 0, sizeof(unsigned int), s));
     k_rows<MODE><<<blocks, RX_THREADS, sm, s>>>(g->rowptr, g->upper, g->col, g->oshift, g->n, sup,
                                                 off, top, pairs, next_row, partials, lc,
-                                                max_pos);
+                                                max_pos, bound);
     TC_LAUNCH_CHECK("k_rows");
     return TC_OK;
 }
@@ -832,7 +1024,9 @@ int ensure_cols_smem_limit() {
 
 template <int MODE>
 int launch_cols(Graph* g, int32_t* sup, const unsigned long long* off, unsigned int* top,
-                int2* pairs, unsigned long long* partials, int blocks, cudaStream_t s) {
+                int2* pairs, unsigned long long* partials, int blocks, cudaStream_t s,
+                int32_t bound = 0, const unsigned int* lowbits = nullptr,
+                const unsigned int* lowpos = nullptr, const int2* lowlist = nullptr) {
     TC_TRY(ensure_cols_smem_limit());
     if (g->max_out > RX_MAX_OUT) return fail(TC_EINVAL, "internal: column kernel above its table size");
     const int lc = rows_log_cap(g);
@@ -841,7 +1035,7 @@ int launch_cols(Graph* g, int32_t* sup, const unsigned long long* off, unsigned 
     unsigned int* next = reinterpret_cast<unsigned int*>(g->dev_scalars + 5);
     TC_CUDA_TRY(cudaMemsetAsync(next, 0, 2 * sizeof(unsigned int), s));
     ColArgs a{g->rowptr, g->upper, g->col, g->eid, g->oshift, g->n, g->light_rows, sup, off, top,
-              pairs, next, partials, lc, max_pos, g->dev_err};
+              pairs, next, partials, lc, max_pos, g->dev_err, bound, lowbits, lowpos, lowlist};
     k_cols<MODE><<<blocks, RX_THREADS, sm, s>>>(a);
     TC_LAUNCH_CHECK("k_cols");
     return TC_OK;
@@ -887,16 +1081,17 @@ int rows_blocks(Graph* g, int mode) {
 
 int graph_wedge_work(Graph* g, int64_t* out, cudaStream_t s) {
     if (g->wedge_work < 0) {
-        unsigned long long h = 0;
+        unsigned long long h[2] = {0, 0};
         if (g->m > 0) {
-            TC_CUDA_TRY(cudaMemsetAsync(g->dev_scalars + 2, 0, sizeof(unsigned long long), s));
-            k_wedge_work<<<num_sms() * 8, 256, 0, s>>>(g->ends, g->rowptr, g->upper, g->m,
+            TC_CUDA_TRY(cudaMemsetAsync(g->dev_scalars + 2, 0, 2 * sizeof(unsigned long long), s));
+            k_wedge_work<<<num_sms() * 8, 256, 0, s>>>(g->ends, g->rowptr, g->upper, g->m, g->n,
                                                        g->dev_scalars + 2);
             TC_LAUNCH_CHECK("k_wedge_work");
-            TC_CUDA_TRY(cudaMemcpyAsync(&h, g->dev_scalars + 2, sizeof(h), cudaMemcpyDeviceToHost, s));
+            TC_CUDA_TRY(cudaMemcpyAsync(h, g->dev_scalars + 2, sizeof(h), cudaMemcpyDeviceToHost, s));
             TC_CUDA_TRY(cudaStreamSynchronize(s));
         }
-        g->wedge_work = (int64_t)h;
+        g->wedge_work = (int64_t)h[0];
+        g->column_work = (int64_t)h[1];
     }
     *out = g->wedge_work;
     return TC_OK;
@@ -930,6 +1125,7 @@ int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangle
     }
     const int f = concrete_form(g, form);
     const int blocks = product_blocks(g, f, want_support ? SUPPORT : COUNT);
+    g->stats.product_form = f;
     Scratch sc(s);
     unsigned long long* partials;
     TC_TRY(sc.alloc(&partials, blocks));
@@ -947,11 +1143,12 @@ int compute_support(Graph* g, int32_t* sup, bool want_support, int64_t* triangle
     } else if (f == 3) {
         if (want_support)
             k_edges_thread<SUPPORT><<<blocks, IX_THREADS, 0, s>>>(
-                g->ends, g->rowptr, g->upper, g->col, g->oshift, m, sup, nullptr, nullptr, partials);
+                g->ends, g->rowptr, g->upper, g->col, g->oshift, m, sup, nullptr, nullptr, partials,
+                0);
         else
             k_edges_thread<COUNT><<<blocks, IX_THREADS, 0, s>>>(
                 g->ends, g->rowptr, g->upper, g->col, g->oshift, m, nullptr, nullptr, nullptr,
-                partials);
+                partials, 0);
         TC_LAUNCH_CHECK("k_edges_thread");
     } else if (want_support) {
         k_edges_warp<true><<<blocks, IX_THREADS, 0, s>>>(g->ends, g->rowptr, g->upper,
@@ -1004,12 +1201,29 @@ int exclusive_scan_i32(const int32_t* x, int64_t n, unsigned long long* out, Scr
     const int64_t chunks = (n + SC_CHUNK - 1) / SC_CHUNK;
     unsigned long long* sums;
     TC_TRY(sc.alloc(&sums, chunks));
-    k_chunk_sums<<<(unsigned)chunks, SC_THREADS, 0, s>>>(x, n, sums);
+    k_chunk_sums<<<(unsigned)chunks, SC_THREADS, 0, s>>>(x, n, 0, sums);
     TC_LAUNCH_CHECK("k_chunk_sums");
     k_scan_sums64<<<1, 1024, 0, s>>>(sums, chunks);
     TC_LAUNCH_CHECK("k_scan_sums64");
-    k_chunk_scan<<<(unsigned)chunks, SC_THREADS, 0, s>>>(x, n, sums, out);
+    k_chunk_scan<<<(unsigned)chunks, SC_THREADS, 0, s>>>(x, n, 0, sums, out);
     TC_LAUNCH_CHECK("k_chunk_scan");
+    return TC_OK;
+}
+
+int partial_list_entries(Graph* g, int32_t bound, int64_t* entries, int64_t* low_edges,
+                         cudaStream_t s) {
+    unsigned long long h[2] = {0, 0};
+    if (g->m > 0) {
+        unsigned long long* d = g->dev_scalars + 6;
+        TC_CUDA_TRY(cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), s));
+        k_low_sums<<<(unsigned)std::min<int64_t>((g->m + 255) / 256, (int64_t)num_sms() * 8), 256, 0,
+                     s>>>(g->support, g->m, bound, d);
+        TC_LAUNCH_CHECK("k_low_sums");
+        TC_CUDA_TRY(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
+        TC_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    *entries = (int64_t)h[0];
+    if (low_edges) *low_edges = (int64_t)h[1];
     return TC_OK;
 }
 
@@ -1018,6 +1232,13 @@ int plan_triangle_lists(Graph* g, Scratch& sc, ListsPlan* lp) {
     lp->chunks = (m + SC_CHUNK - 1) / SC_CHUNK;
     TC_TRY(sc.alloc(&lp->sums, lp->chunks));
     TC_TRY(sc.alloc(&lp->top, m));
+    if (lp->bound > 0) {
+        // the column kernel's low edges: bits, positions, compacted list
+        TC_TRY(sc.alloc(&lp->lowbits, m / 32 + 1));
+        TC_TRY(sc.alloc(&lp->lowpos, m + 1));
+        TC_TRY(sc.alloc(&lp->lowsums, lp->chunks));
+        TC_TRY(sc.alloc(&lp->lowlist, std::max<int64_t>(1, lp->low_edges)));
+    }
     lp->form = concrete_form(g, 0);
     if (lp->form == 2) lp->form = 1;  // lists need a table kernel (the caller checked the size)
     lp->thread = lp->form == 3;
@@ -1033,25 +1254,38 @@ int plan_triangle_lists(Graph* g, Scratch& sc, ListsPlan* lp) {
 int enqueue_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off, int2* pairs,
                            ListsPlan* lp, cudaStream_t s) {
     const int64_t m = g->m;
-    k_chunk_sums<<<(unsigned)lp->chunks, SC_THREADS, 0, s>>>(sup, m, lp->sums);
+    k_chunk_sums<<<(unsigned)lp->chunks, SC_THREADS, 0, s>>>(sup, m, lp->bound, lp->sums);
     TC_LAUNCH_CHECK("k_chunk_sums");
     k_scan_sums64<<<1, 1024, 0, s>>>(lp->sums, lp->chunks);
     TC_LAUNCH_CHECK("k_scan_sums64");
-    k_chunk_scan<<<(unsigned)lp->chunks, SC_THREADS, 0, s>>>(sup, m, lp->sums, off);
+    k_chunk_scan<<<(unsigned)lp->chunks, SC_THREADS, 0, s>>>(sup, m, lp->bound, lp->sums, off);
     TC_LAUNCH_CHECK("k_chunk_scan");
+    if (lp->bound > 0 && lp->form == 1) {
+        k_low_chunk_counts<<<(unsigned)lp->chunks, SC_THREADS, 0, s>>>(sup, m, lp->bound,
+                                                                      lp->lowbits, lp->lowsums);
+        TC_LAUNCH_CHECK("k_low_chunk_counts");
+        k_scan_sums64<<<1, 1024, 0, s>>>(lp->lowsums, lp->chunks);
+        TC_LAUNCH_CHECK("k_scan_sums64");
+        k_low_scan<<<(unsigned)lp->chunks, SC_THREADS, 0, s>>>(sup, g->ends, m, lp->bound,
+                                                              lp->lowsums, lp->lowpos, lp->lowlist);
+        TC_LAUNCH_CHECK("k_low_scan");
+    }
     k_u32_from_u64<<<(unsigned)std::min<int64_t>((m + 255) / 256, (int64_t)num_sms() * 16), 256, 0,
                      s>>>(off + 1, m, lp->top);
     TC_LAUNCH_CHECK("k_u32_from_u64");
     TC_TRY(lp->timer.start(s));
+    int32_t* sup_rw = const_cast<int32_t*>(sup);  // read-only in LISTS mode
     if (lp->thread) {
         k_edges_thread<LISTS><<<lp->blocks, IX_THREADS, 0, s>>>(
-            g->ends, g->rowptr, g->upper, g->col, g->oshift, m, nullptr, lp->top, pairs,
-            lp->partials);
+            g->ends, g->rowptr, g->upper, g->col, g->oshift, m, sup_rw, lp->top, pairs,
+            lp->partials, lp->bound);
         TC_LAUNCH_CHECK("k_edges_thread");
     } else if (lp->form == 4) {
-        TC_TRY(launch_rows<LISTS>(g, nullptr, off, lp->top, pairs, lp->partials, lp->blocks, s));
+        TC_TRY(launch_rows<LISTS>(g, sup_rw, off, lp->top, pairs, lp->partials, lp->blocks, s,
+                                  lp->bound));
     } else {
-        TC_TRY(launch_cols<LISTS>(g, nullptr, off, lp->top, pairs, lp->partials, lp->blocks, s));
+        TC_TRY(launch_cols<LISTS>(g, sup_rw, off, lp->top, pairs, lp->partials, lp->blocks, s,
+                                  lp->bound, lp->lowbits, lp->lowpos, lp->lowlist));
     }
     TC_TRY(lp->timer.stop(s));
     return TC_OK;

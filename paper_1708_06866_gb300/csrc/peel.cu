@@ -59,6 +59,9 @@ constexpr int64_t SHORT_LIST = TC_PK_SHORT_LIST;
 #ifndef TC_PK_UNROLL
 #define TC_PK_UNROLL 3               // triangle-list entries per lane in flight
 #endif
+#ifndef TC_PK_SCAN_UNROLL
+#define TC_PK_SCAN_UNROLL 4          // level scan: 32-edge chunks per warp iteration
+#endif
 
 struct PeelCtl {
     unsigned long long bar;      // grid-barrier arrivals (monotonic)
@@ -164,24 +167,6 @@ __device__ bool grid_sync(PeelCtl* ctl, unsigned long long* epoch, int64_t spin_
     return *s_ok != 0;
 }
 
-__device__ __forceinline__ void warp_append(bool take, int32_t value, int32_t* list,
-                                            unsigned long long* counter,
-                                            unsigned long long base, uint2* ranges = nullptr,
-                                            uint2 range = uint2{}) {
-    const unsigned mask = __ballot_sync(0xffffffffu, take);
-    if (mask == 0) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(mask) - 1;
-    unsigned long long pos = 0;
-    if (lane == leader) pos = atomicAdd(counter, (unsigned long long)__popc(mask));
-    pos = __shfl_sync(0xffffffffu, pos, leader);
-    if (take) {
-        const unsigned long long q = pos - base + __popc(mask & lanemask_lt());
-        list[q] = value;
-        if (ranges) ranges[q] = range;
-    }
-}
-
 // Edge states during round r: 0 = alive; -r = in round r's frontier (dying);
 // -(r + 1) = alive, already in the next frontier; -q with q < r = removed in
 // round q.  Stamping states with round numbers needs no pass that retires a
@@ -269,17 +254,19 @@ __device__ __forceinline__ void destroy(const PeelArgs& a, Round rd, int32_t e, 
 }
 
 // All triangles through frontier edge e, by a group of gsize lanes (rg: its
-// triangle-list range, list form only).  The edge's current support is
+// triangle-list range, when lists exist).  The edge's current support is
 // exactly its number of live triangles (those whose other two edges are not
 // removed): support 0 means nothing to do, and a single-warp group stops
-// once it has seen them all.
-template <bool TL>
+// once it has seen them all.  TL: edges have triangle lists (with IX, only
+// some do: an edge with live triangles and an empty range has none);
+// IX: the live neighbour lists are kept for intersecting.
+template <bool TL, bool IX>
 __device__ __forceinline__ void process_edge(const PeelArgs& a, Round rd, int32_t e, uint2 rg,
                                              int64_t glane, int64_t gsize, const Sinks& k,
                                              Tally& tl) {
     const bool one_warp = gsize == 32;
     int32_t seen = 0;  // live triangles met so far (one_warp only; warp-uniform)
-    if (TL) {
+    if (TL && (!IX || rg.y > rg.x)) {
         const int64_t q0 = rg.x, q1 = rg.y;
         const int32_t live = ld_cg(a.s + e);
         if (live <= 0) return;
@@ -342,6 +329,7 @@ __device__ __forceinline__ void process_edge(const PeelArgs& a, Round rd, int32_
         }
         return;
     }
+    if (!IX) return;
     const int32_t live = ld_cg(a.s + e);
     if (live <= 0) return;
     const int2 ab = a.ends[e];
@@ -393,29 +381,31 @@ __device__ __forceinline__ void process_edge(const PeelArgs& a, Round rd, int32_
 // Groups of W warps per edge (W a power of two, as wide as the list count
 // allows, spanning blocks when the list is short); each group takes edges
 // round-robin.
-template <bool TL>
+template <bool TL, bool IX>
 __device__ __forceinline__ void process_list(const PeelArgs& a, Round rd, const int32_t* L,
                                              const uint2* LR, int64_t nL, int64_t gwarp,
                                              int64_t nwarps, const Sinks& k, Tally& tl) {
     if (nL == 0) return;
     if (TL && nL >= nwarps * LANE_EDGES) {
         // many edges per warp: each lane takes one; lists of up to
-        // SHORT_LIST entries are walked by their lane alone, longer ones by
-        // the whole warp, one after another
+        // SHORT_LIST entries are walked by their lane alone, longer ones (and,
+        // with IX, edges without a list, whose neighbour lists are
+        // intersected) by the whole warp, one after another
         const int lane = threadIdx.x & 31;
         for (int64_t base = gwarp * 32; base < nL; base += nwarps * 32) {
             const int64_t j = base + lane;
             const int32_t e = j < nL ? ld_cg(L + j) : -1;
             const uint2 rg = j < nL ? __ldcg(LR + j) : make_uint2(0, 0);
-            const bool longer = e >= 0 && (int64_t)(rg.y - rg.x) > SHORT_LIST;
-            if (e >= 0 && !longer) process_edge<TL>(a, rd, e, rg, 0, 1, k, tl);
+            const bool longer =
+                e >= 0 && ((int64_t)(rg.y - rg.x) > SHORT_LIST || (IX && rg.y == rg.x));
+            if (e >= 0 && !longer) process_edge<TL, IX>(a, rd, e, rg, 0, 1, k, tl);
             unsigned rest = __ballot_sync(0xffffffffu, longer);
             while (rest) {
                 const int src = __ffs(rest) - 1;
                 rest &= rest - 1;
                 const uint2 rs = make_uint2(__shfl_sync(0xffffffffu, rg.x, src),
                                             __shfl_sync(0xffffffffu, rg.y, src));
-                process_edge<TL>(a, rd, __shfl_sync(0xffffffffu, e, src), rs, lane, 32, k, tl);
+                process_edge<TL, IX>(a, rd, __shfl_sync(0xffffffffu, e, src), rs, lane, 32, k, tl);
             }
         }
         return;
@@ -427,8 +417,8 @@ __device__ __forceinline__ void process_list(const PeelArgs& a, Round rd, const 
     if (group >= ngroups) return;
     const int64_t glane = (gwarp % W) * 32 + (threadIdx.x & 31);
     for (int64_t j = group; j < nL; j += ngroups)
-        process_edge<TL>(a, rd, ld_cg(L + j), TL ? __ldcg(LR + j) : make_uint2(0, 0), glane,
-                         32 * W, k, tl);
+        process_edge<TL, IX>(a, rd, ld_cg(L + j), TL ? __ldcg(LR + j) : make_uint2(0, 0), glane,
+                             32 * W, k, tl);
 }
 
 // The peel.  Levels k = k_first, k_first + 1, ...; each level starts with a
@@ -441,9 +431,11 @@ __device__ __forceinline__ void process_list(const PeelArgs& a, Round rd, const 
 // the window at that moment.  Once the threshold passes the bound, the next
 // level makes a full scan again.
 //
-// TL = true: each edge's triangles come from its precomputed triangle list;
-// TL = false: from the intersection of its endpoints' live neighbour lists.
-template <bool TL>
+// TL: an edge's triangles come from its precomputed triangle list; IX:
+// from the intersection of its endpoints' live neighbour lists.  Both: the
+// list when the edge has one (lists were built only for edges whose support
+// was below a bound), else the intersection.
+template <bool TL, bool IX>
 __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
     __shared__ int s_ok;
     unsigned long long epoch = 0;
@@ -489,36 +481,125 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
             // the slot the level after next uses: clear it for that level
             if (leader) ctl->minenc[(level + 1) % 3] = 0;
             int smin = INT_MAX;  // smallest support among the alive edges scanned
-            for (int64_t base = gwarp * 32; base < n_in; base += nwarps * 32) {
-                const int64_t i = base + lane;
-                bool alive = false, win = false, light = false, heavy = false;
-                int32_t e = 0;
-                uint2 rg = make_uint2(0, 0);
-                if (i < n_in) {
-                    ++tl.scanned;
-                    e = in ? ld_cg(in + i) : (int32_t)i;
+            // Two passes over the warp's share: the first classifies every
+            // scanned edge (marking the frontier) and counts what each list
+            // receives; one atomic per warp and list then reserves the
+            // ranges, and the second pass writes the entries.  (An append per
+            // 32 edges serialised millions of atomics on one counter in a
+            // full scan.)  A call that peels one level never scans again: it
+            // needs neither the alive list (only its length) nor the window.
+            const bool wantA = full && !a.single, wantW = !a.single;
+            // SU chunks of 32 edges per warp iteration, all loads in flight
+            // before any is used (the scan is bound by load latency)
+            constexpr int SU = TC_PK_SCAN_UNROLL;
+            const int64_t wstep = nwarps * 32 * SU;
+            unsigned long long cA = 0, cW = 0, cF = 0, cH = 0;
+            for (int64_t base = gwarp * 32 * SU; base < n_in; base += wstep) {
+                int32_t e[SU], te[SU], se[SU];
+#pragma unroll
+                for (int u = 0; u < SU; ++u) {
+                    const int64_t i = base + 32 * u + lane;
+                    e[u] = i < n_in ? (in ? ld_cg(in + i) : (int32_t)i) : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < SU; ++u) {
                     // state and support loaded together (scanned edges are
                     // mostly alive)
-                    const int32_t te = ld_cg(a.t + e), se = ld_cg(a.s + e);
-                    alive = te == 0;
-                    if (alive) {
-                        smin = min(smin, se);
-                        win = se < bound;
-                        if (se < thr) {
-                            a.t[e] = -r;
-                            if (TL) rg = list_range(a, e);
-                            heavy = TL && is_heavy(rg);
-                            light = !heavy;
+                    te[u] = e[u] >= 0 ? ld_cg(a.t + e[u]) : 1;
+                    se[u] = e[u] >= 0 ? ld_cg(a.s + e[u]) : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < SU; ++u) {
+                    bool alive = false, win = false, light = false, heavy = false;
+                    if (e[u] >= 0) {
+                        ++tl.scanned;
+                        alive = te[u] == 0;
+                        if (alive) {
+                            smin = min(smin, se[u]);
+                            win = se[u] < bound;
+                            if (se[u] < thr) {
+                                a.t[e[u]] = -r;
+                                heavy = TL && is_heavy(list_range(a, e[u]));
+                                light = !heavy;
+                            }
                         }
                     }
+                    cA += __popc(__ballot_sync(0xffffffffu, alive));
+                    cW += __popc(__ballot_sync(0xffffffffu, win));
+                    cF += __popc(__ballot_sync(0xffffffffu, light));
+                    cH += __popc(__ballot_sync(0xffffffffu, heavy));
                 }
-                if (full) warp_append(alive, e, Aout, &ctl->cntA[pa], baseA[pa]);
-                warp_append(win, e, Wout, &ctl->cntW[wp], baseW[wp]);
-                warp_append(light, e, a.F[fi], &ctl->cntF[pf], baseF[pf], a.FR[fi], rg);
-                warp_append(heavy, e, a.H[fi], &ctl->cntH[pf], baseH[pf], a.HR[fi], rg);
             }
             smin = __reduce_min_sync(0xffffffffu, smin);
             if (lane == 0 && smin != INT_MAX) atomicMax(&ctl->minenc[ms], INT_MAX - smin);
+            unsigned long long rA = 0, rW = 0, rF = 0, rH = 0;
+            if (lane == 0) {
+                if (full && cA) rA = atomicAdd(&ctl->cntA[pa], cA);
+                if (wantW && cW) rW = atomicAdd(&ctl->cntW[wp], cW);
+                if (cF) rF = atomicAdd(&ctl->cntF[pf], cF);
+                if (cH) rH = atomicAdd(&ctl->cntH[pf], cH);
+            }
+            rA = __shfl_sync(0xffffffffu, rA, 0) - baseA[pa];
+            rW = __shfl_sync(0xffffffffu, rW, 0) - baseW[wp];
+            rF = __shfl_sync(0xffffffffu, rF, 0) - baseF[pf];
+            rH = __shfl_sync(0xffffffffu, rH, 0) - baseH[pf];
+            if ((wantA && cA) || (wantW && cW) || cF || cH) {
+                for (int64_t base = gwarp * 32 * SU; base < n_in; base += wstep) {
+                    int32_t e[SU], te[SU];
+#pragma unroll
+                    for (int u = 0; u < SU; ++u) {
+                        const int64_t i = base + 32 * u + lane;
+                        e[u] = i < n_in ? (in ? ld_cg(in + i) : (int32_t)i) : -1;
+                    }
+#pragma unroll
+                    for (int u = 0; u < SU; ++u) te[u] = e[u] >= 0 ? ld_cg(a.t + e[u]) : 1;
+#pragma unroll
+                    for (int u = 0; u < SU; ++u) {
+                        bool alive = false, win = false, light = false, heavy = false;
+                        uint2 rg = make_uint2(0, 0);
+                        if (e[u] >= 0) {
+                            // this scan's frontier carries the (fresh) round number
+                            const bool front = te[u] == -r;
+                            alive = te[u] == 0 || front;
+                            if (alive && wantW) win = ld_cg(a.s + e[u]) < bound;
+                            if (front) {
+                                if (TL) rg = list_range(a, e[u]);
+                                heavy = TL && is_heavy(rg);
+                                light = !heavy;
+                            }
+                        }
+                        const unsigned lt = lanemask_lt();
+                        if (wantA) {
+                            const unsigned mk = __ballot_sync(0xffffffffu, alive);
+                            if (alive) Aout[rA + __popc(mk & lt)] = e[u];
+                            rA += __popc(mk);
+                        }
+                        if (wantW) {
+                            const unsigned mk = __ballot_sync(0xffffffffu, win);
+                            if (win) Wout[rW + __popc(mk & lt)] = e[u];
+                            rW += __popc(mk);
+                        }
+                        {
+                            const unsigned mk = __ballot_sync(0xffffffffu, light);
+                            if (light) {
+                                const unsigned long long q = rF + __popc(mk & lt);
+                                a.F[fi][q] = e[u];
+                                if (TL) a.FR[fi][q] = rg;
+                            }
+                            rF += __popc(mk);
+                        }
+                        {
+                            const unsigned mk = __ballot_sync(0xffffffffu, heavy);
+                            if (heavy) {
+                                const unsigned long long q = rH + __popc(mk & lt);
+                                a.H[fi][q] = e[u];
+                                if (TL) a.HR[fi][q] = rg;
+                            }
+                            rH += __popc(mk);
+                        }
+                    }
+                }
+            }
         }
         if (!grid_sync(ctl, &epoch, a.spin_ns, &s_ok)) return;
         if (full) {
@@ -560,9 +641,9 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
             if (leader) a.level_of[r + 1] = k;
             const Sinks sk{a.F[fi ^ 1], a.H[fi ^ 1], a.FR[fi ^ 1], a.HR[fi ^ 1], Wout,
                            &ctl->cntF[pn], &ctl->cntH[pn], &ctl->cntW[wp], baseF[pn],
-                           baseH[pn], baseW[wp], thr, bound};
-            process_list<TL>(a, rd, a.F[fi], a.FR[fi], nF, gwarp, nwarps, sk, tl);
-            process_list<TL>(a, rd, a.H[fi], a.HR[fi], nH, gwarp, nwarps, sk, tl);
+                           baseH[pn], baseW[wp], thr, a.single ? INT_MIN : bound};
+            process_list<TL, IX>(a, rd, a.F[fi], a.FR[fi], nF, gwarp, nwarps, sk, tl);
+            process_list<TL, IX>(a, rd, a.H[fi], a.HR[fi], nH, gwarp, nwarps, sk, tl);
             if (!grid_sync(ctl, &epoch, a.spin_ns, &s_ok)) return;
             const unsigned long long eF = ld_vol(&ctl->cntF[pn]), eH = ld_vol(&ctl->cntH[pn]);
             n_alive -= nF + nH;
@@ -573,7 +654,7 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
             fi ^= 1;
             ++r;
             // compact the rows once half of their entries are removed edges
-            if (!TL && 4 * n_alive < nnz) {
+            if (IX && 4 * n_alive < nnz) {
                 ++compactions;
                 const Round now{r};
                 for (int64_t row = gwarp; row < a.n; row += nwarps) {
@@ -692,7 +773,9 @@ inline unsigned small_grid(int64_t items) {
 struct PeelPlan {
     Graph* g = nullptr;
     PeelArgs a{};
-    bool tl = false;
+    bool tl = false;           // triangle lists (all edges, or with ix those below bound)
+    bool ix = true;            // live neighbour lists kept for intersections
+    int32_t bound = 0;         // lists only for edges whose support is below it (0: all)
     bool single = false;
     const void* fn = nullptr;
     int blocks = 0;
@@ -715,9 +798,10 @@ PeelPlan* peel_plan_new() { return new (std::nothrow) PeelPlan(); }
 namespace {
 // Optional memory the graph keeps now: triangle lists, the compacted
 // adjacency of the latest k-truss, truss numbers.
-double lists_bytes(const Graph* g) {
-    return 24.0 * (double)std::max<int64_t>(g->triangles, 0) + 8.0 * (double)(g->m + 1);
+double lists_bytes(const Graph* g, int64_t entries) {
+    return 8.0 * (double)std::max<int64_t>(entries, 0) + 8.0 * (double)(g->m + 1);
 }
+double lists_bytes(const Graph* g) { return lists_bytes(g, g->tri_entries); }
 double adj_bytes(const Graph* g) { return 16.0 * (double)g->m + 4.0 * (double)g->n; }
 double kept_optional_bytes(const Graph* g) {
     return (g->tri_off ? lists_bytes(g) : 0.0) + (g->kt_col ? adj_bytes(g) : 0.0) +
@@ -762,22 +846,44 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
     }
     const int forced = form != PEEL_AUTO ? form : peel_mode();
     p.tl = false;
-    // list positions are 32-bit: the triangle-list form needs 3T < 2^32
+    p.ix = true;
+    p.bound = 0;
     size_t free_b = 0, total_b = 0;
     TC_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     // optional memory (lists, caches) stays within the graph's bound, all of
-    // it together, or a share of the free memory when the caller set none
-    if (triangle_lists_supported(g) && forced != PEEL_INTERSECT &&
-        3 * g->triangles < 0xffffffffLL) {
-        p.tl = forced == PEEL_LISTS ||
-               may_keep(g, lists_bytes(g), g->tri_off != nullptr, 0.6 * (double)free_b);
+    // it together, or a share of the free memory when the caller set none.
+    // List positions are 32-bit: full lists need 3T < 2^32, partial lists
+    // (edges whose support is below LIST_BOUND) fewer than 2^32 entries.
+    int64_t entries = 0;
+    if (triangle_lists_supported(g) && forced != PEEL_INTERSECT) {
+        const int64_t full = 3 * std::max<int64_t>(g->triangles, 0);
+        const bool held_full = g->tri_off && g->tri_bound == 0;
+        if (full < 0xffffffffLL && forced != PEEL_HYBRID &&
+            (forced == PEEL_LISTS ||
+             may_keep(g, lists_bytes(g, full), held_full, 0.6 * (double)free_b))) {
+            p.tl = true;
+            p.ix = false;
+            entries = full;
+        } else if (forced != PEEL_LISTS || full >= 0xffffffffLL) {
+            TC_TRY(partial_list_entries(g, LIST_BOUND, &entries, &p.lists.low_edges,
+                                        g->last_stream));
+            const bool held = g->tri_off && g->tri_bound == LIST_BOUND;
+            if (entries < 0xffffffffLL &&
+                (forced == PEEL_HYBRID ||
+                 may_keep(g, lists_bytes(g, entries), held, 0.6 * (double)free_b))) {
+                p.tl = true;
+                p.bound = LIST_BOUND;
+            }
+        }
     }
-    if (!p.tl && g->tri_off) {  // cached lists above a lowered limit are dropped
+    if (g->tri_off && (!p.tl || g->tri_bound != p.bound)) {
+        // cached lists above a lowered limit, or of the other kind, are dropped
         dev_free(g->tri_off, g->last_stream);
         dev_free(g->tri_pairs, g->last_stream);
         g->tri_off = nullptr;
         g->tri_pairs = nullptr;
         g->tri_valid = false;
+        g->tri_entries = 0;
     }
     if (p.tl && g->tri_valid) {
         p.off = g->tri_off;  // built by an earlier peel of this graph
@@ -790,18 +896,24 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
         p.keep_lists = keep_lists;
         if (keep_lists) {
             if (!g->tri_off) TC_TRY(dev_alloc_n(&g->tri_off, m + 1, g->last_stream));
-            if (!g->tri_pairs)
-                TC_TRY(dev_alloc_n(&g->tri_pairs, std::max<int64_t>(1, 3 * g->triangles),
-                                   g->last_stream));
+            if (!g->tri_pairs) {
+                TC_TRY(dev_alloc_n(&g->tri_pairs, std::max<int64_t>(1, entries), g->last_stream));
+                g->tri_entries = entries;
+                g->tri_bound = p.bound;
+            }
             p.off = g->tri_off;
             p.pairs = g->tri_pairs;
         } else {
             TC_TRY(sc.alloc(&p.off, m + 1));
-            TC_TRY(sc.alloc(&p.pairs, std::max<int64_t>(1, 3 * g->triangles)));
+            TC_TRY(sc.alloc(&p.pairs, std::max<int64_t>(1, entries)));
         }
+        p.lists.bound = p.bound;
         TC_TRY(plan_triangle_lists(g, sc, &p.lists));
         a.off = p.off;
         a.pairs = p.pairs;
+    }
+    if (!p.ix) {
+        // list form only: no adjacency
     } else if (p.cache) {
         // the compacted adjacency stays with the graph when it fits
         p.fresh_adj = !(p.resume && g->kt_adj);
@@ -838,9 +950,9 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
     }
     if (p.cache) a.s = g->kt_support;
     else TC_TRY(sc.alloc(&a.s, m));
-    // a heavy edge has more than HEAVY of the 3T list entries (the
+    // a heavy edge has more than HEAVY of the list entries (the
     // intersection form has none)
-    const int64_t heavy_cap = p.tl ? std::min<int64_t>(m, 3 * g->triangles / HEAVY + 1) : 1;
+    const int64_t heavy_cap = p.tl ? std::min<int64_t>(m, entries / HEAVY + 1) : 1;
     for (int i = 0; i < 2; ++i) {
         TC_TRY(sc.alloc(&a.A[i], m));
         TC_TRY(sc.alloc(&a.W[i], m));
@@ -860,7 +972,8 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
     // ever runs out.
     a.max_round = std::min<int64_t>(m + 2 * (int64_t)g->max_deg + 64, 0x7fffffffLL - 16);
     TC_TRY(sc.alloc(&a.level_of, a.max_round));
-    p.fn = p.tl ? (const void*)k_peel<true> : (const void*)k_peel<false>;
+    p.fn = !p.tl ? (const void*)k_peel<false, true>
+           : p.ix ? (const void*)k_peel<true, true> : (const void*)k_peel<true, false>;
     int per_sm = 0;
     TC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p.fn, PK_THREADS, 0));
     if (per_sm < 1) return fail(TC_ECUDA, "k_peel cannot be resident");
@@ -871,7 +984,7 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
                                            TC_PK_MAX_BLOCKS);
     p.blocks = (int)std::min<int64_t>(want, (int64_t)num_sms() * std::min(per_sm, 1024 / PK_THREADS));
     if (max_blocks > 0) p.blocks = std::min(p.blocks, max_blocks);
-    g->last_peel_lists = p.tl;
+    g->last_peel_lists = p.tl ? (p.ix ? 2 : 1) : 0;
     return TC_OK;
 }
 
@@ -880,10 +993,9 @@ int peel_enqueue(PeelPlan* pp, cudaStream_t s) {
     Graph* g = p.g;
     PeelArgs& a = p.a;
     const int64_t m = g->m;
-    if (p.tl) {
-        if (p.build_lists)
-            TC_TRY(enqueue_triangle_lists(g, g->support, p.off, p.pairs, &p.lists, s));
-    } else if (p.fresh_adj) {
+    if (p.tl && p.build_lists)
+        TC_TRY(enqueue_triangle_lists(g, g->support, p.off, p.pairs, &p.lists, s));
+    if (p.ix && p.fresh_adj) {
         TC_CUDA_TRY(cudaMemcpyAsync(a.col, g->col, sizeof(int32_t) * 2 * m,
                                     cudaMemcpyDeviceToDevice, s));
         TC_CUDA_TRY(cudaMemcpyAsync(a.eid, g->eid, sizeof(int32_t) * 2 * m,
@@ -945,14 +1057,15 @@ int peel_finish(PeelPlan* pp, cudaStream_t s, int64_t* n_alive, int32_t* kmax) {
     if (p.build_lists && p.keep_lists) g->tri_valid = true;
     if (p.cache) {
         g->kt_k = p.a.k_first;
-        g->kt_adj = !p.tl && p.a.col == g->kt_col && g->kt_col != nullptr;
+        g->kt_adj = p.ix && p.a.col == g->kt_col && g->kt_col != nullptr;
     }
     if (n_alive) *n_alive = r.n_alive;
     if (kmax) *kmax = r.kmax;
     return TC_OK;
 }
 
-bool peel_uses_lists(const PeelPlan* p) { return p->tl; }
+bool peel_uses_lists(const PeelPlan* p) { return p->tl && !p->ix; }
+int peel_form_of(const PeelPlan* p) { return p->tl ? (p->ix ? PEEL_HYBRID : PEEL_LISTS) : PEEL_INTERSECT; }
 
 namespace {
 

@@ -354,10 +354,10 @@ int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream) {
     // lo, hi, ends, inv (m each) and col, eid (2m each); rowptr, upper, oshift
     info->device_bytes = m * (4 + 4 + 8 + 4 + 8 + 8) + 8 * (n + 1) + 8 * n + 8 * n +
                          (gg->support ? 4 * m : 0) +
-                         (gg->tri_valid ? 8 * (m + 1) + 24 * gg->triangles : 0) +
+                         (gg->tri_valid ? 8 * (m + 1) + 8 * gg->tri_entries : 0) +
                          (gg->kt_state ? 8 * m : 0) + (gg->truss_cache ? 4 * m : 0) + (gg->kt_col ? 16 * m + 4 * n : 0);
     info->peel_rounds = gg->last_peel_rounds;
-    info->peel_lists = gg->last_peel_lists ? 1 : 0;
+    info->peel_lists = gg->last_peel_lists;
     info->count_kernel_ns = gg->stats.count_ns;
     info->support_kernel_ns = gg->stats.support_ns;
     info->lists_kernel_ns = gg->stats.lists_ns;
@@ -369,6 +369,8 @@ int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream) {
     info->peel_lookups = gg->stats.peel_lookups;
     info->peel_lowered = gg->stats.peel_lowered;
     info->truss_cached = gg->truss_valid ? 1 : 0;
+    info->column_work = gg->column_work;
+    info->product_form = gg->stats.product_form;
     return TC_OK;
 }
 
@@ -419,7 +421,7 @@ int tc_debug_intersect_mode(int mode) {
 }
 
 int tc_debug_peel_mode(int mode) {
-    if (mode < 0 || mode > 2) return tc::g_peel_mode.load();
+    if (mode < 0 || mode > 3) return tc::g_peel_mode.load();
     return tc::g_peel_mode.exchange(mode);
 }
 

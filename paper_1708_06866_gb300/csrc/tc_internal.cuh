@@ -48,10 +48,19 @@ int64_t spin_limit_ns();
 
 // Columns of the masked product whose vertex has at most this degree are
 // processed by one warp each (warp-private table); the others by one block.
-constexpr int LIGHT_DEG = 64;
+#ifndef TC_LIGHT_DEG
+#define TC_LIGHT_DEG 128
+#endif
+constexpr int LIGHT_DEG = TC_LIGHT_DEG;
 
 // Which form of the peel to use (test hook; PEEL_AUTO by default).
-enum : int { PEEL_AUTO = 0, PEEL_LISTS = 1, PEEL_INTERSECT = 2 };
+// PEEL_HYBRID: triangle lists for the edges whose support is below
+// LIST_BOUND, intersections of live neighbour lists for the others.
+enum : int { PEEL_AUTO = 0, PEEL_LISTS = 1, PEEL_INTERSECT = 2, PEEL_HYBRID = 3 };
+#ifndef TC_LIST_BOUND
+#define TC_LIST_BOUND 8
+#endif
+constexpr int LIST_BOUND = TC_LIST_BOUND;
 int peel_mode();
 // Which count/support kernel to use (test hook): 0 automatic, 1 column
 // kernel where the graph allows it, 2 edge-per-warp binary search, 3 thread
@@ -242,10 +251,12 @@ struct Graph {
     int32_t max_deg = 0;
     int32_t light_rows = 0;   // rows of degree <= LIGHT_DEG (the lowest ranks)
     int64_t wedge_work = -1;  // sum of |N+(u)| + |N+(v)| over oriented edges (lazy)
+    int64_t column_work = -1; // sum over u of |N+(u)| (|N+(u)| - 1) / 2 (lazy, with wedge_work)
     int64_t last_peel_rounds = 0;  // bulk rounds of the most recent peel
-    bool last_peel_lists = false;  // whether it used triangle lists
+    int last_peel_lists = 0;       // 1: it used triangle lists, 2: lists below a bound
     struct {
         int64_t count_ns = -1, support_ns = -1, lists_ns = -1, peel_ns = -1;
+        int64_t product_form = 0;  // masked-product kernel of the latest count/support
         int64_t peel_bytes = -1;
         int64_t peel_scanned = 0, peel_entries = 0, peel_searches = 0, peel_lookups = 0,
                 peel_lowered = 0;
@@ -258,6 +269,8 @@ struct Graph {
     unsigned long long* tri_off = nullptr;
     int2* tri_pairs = nullptr;
     bool tri_valid = false;
+    int32_t tri_bound = 0;     // 0: every edge has its list; B: only edges of support < B
+    int64_t tri_entries = 0;   // pairs allocated
     // the latest single-level k-truss (ktruss): internal edge states (0 = in
     // the truss), supports within it and, for the intersection form, its
     // compacted adjacency; a later ktruss with a k at least as large resumes
@@ -290,6 +303,12 @@ struct ListsPlan {
     unsigned int* top = nullptr;         // per-edge fill positions from the list's end
     bool thread = false;                 // built by the thread-per-edge kernel
     int form = 1;                        // the intersection kernel that builds them
+    int32_t bound = 0;                   // lists only for edges of support < bound (0: all)
+    int64_t low_edges = 0;               // ... edges with support in (0, bound)
+    unsigned int* lowbits = nullptr;     // ... one bit per such edge
+    unsigned int* lowpos = nullptr;      // ... their exclusive prefix count by edge id
+    unsigned long long* lowsums = nullptr;
+    int2* lowlist = nullptr;             // ... {head, edge id} of each, by edge id
     unsigned long long* partials = nullptr;
     int blocks = 0;
     KernelTimer timer;
@@ -298,6 +317,10 @@ int plan_triangle_lists(Graph* g, Scratch& sc, ListsPlan* lp);
 // out[i] = x[0] + ... + x[i-1] for i in [0, n] (n + 1 entries).
 int exclusive_scan_i32(const int32_t* x, int64_t n, unsigned long long* out, Scratch& sc,
                        cudaStream_t s);
+// Sum of the supports in (0, bound) (the entries of lists kept only for
+// those edges) and the number of such edges; synchronises.
+int partial_list_entries(Graph* g, int32_t bound, int64_t* entries, int64_t* low_edges,
+                         cudaStream_t s);
 int enqueue_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off, int2* pairs,
                            ListsPlan* lp, cudaStream_t s);
 
@@ -314,7 +337,8 @@ int peel_plan(PeelPlan* p, Scratch& sc, Graph* g, int32_t k_first, bool single, 
               int form, bool keep_lists = false, bool use_cache = false, int max_blocks = 0);
 int peel_enqueue(PeelPlan* p, cudaStream_t s);
 int peel_finish(PeelPlan* p, cudaStream_t s, int64_t* n_alive, int32_t* kmax);
-bool peel_uses_lists(const PeelPlan* p);
+bool peel_uses_lists(const PeelPlan* p);  // full lists
+int peel_form_of(const PeelPlan* p);      // PEEL_LISTS, PEEL_INTERSECT or PEEL_HYBRID
 int ensure_support(Graph* g, cudaStream_t s);
 // Internal-order per-edge arrays -> canonical order (out[c] = in[inv[c]]: a
 // gather, so the writes are coalesced).

@@ -2,23 +2,18 @@
 
 The 8192 x 8192 image graph (268M edges) is checked in full against the
 closed forms of Section IV-C.  R-MAT scale 24 (268M generated pairs) is
-checked against the oracle on sampled outputs and on properties that hold
-at any size.
-
-The oracle's full truss peel at this size takes hours, so:
-  * the canonical edge list is compared in full (the oracle's cleaning is a
-    sort and a repeat removal);
-  * per-edge supports are compared on a seeded sample of edges, each counted
-    by the oracle one by one; sum of supports = 3 * triangles;
-  * for each k of 3, 4, 6, 8: survivors of the k-truss have support >= k - 2
-    within it and removed edges close < k - 2 triangles with it (maximality),
-    on seeded samples; the trusses nest; the reported size is the mask's.
+checked in full against the oracle's stored results: SHA-256 hashes of the
+canonical edge list, of every per-edge support and of each k-truss mask
+(k = 3, 4, 6, 8), written once by tests/golden/make_oracle_fixtures.py (the
+oracle's serial peel takes over an hour at this size).
 """
+import hashlib
+import os
+
 import numpy as np
 import pytest
 
 import graphgen
-import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -28,52 +23,59 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 import paper_1708_06866_gb300 as tc  # noqa: E402
 
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-def test_rmat24_full_size_sampled_against_oracle():
+
+def _sha(a):
+    return hashlib.sha256(np.ascontiguousarray(a, dtype="<i4").tobytes()).hexdigest()
+
+
+def _fixture(name):
+    out = {}
+    with open(os.path.join(ROOT, "tests", "golden", f"{name}_oracle.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if line:
+                out.setdefault(line[0], []).append(line[1:])
+    return out
+
+
+def test_rmat24_full_size_against_stored_oracle():
+    """The bench's scale-24 sequence (count, supports, then ktruss at
+    k = 3, 4, 6, 8, each call resuming from the previous truss, in the
+    automatic form: triangle lists for the edges of support below the bound,
+    intersections for the rest) equals the oracle bit for bit; so do fresh
+    peels in the intersection form and in the bounded-list form."""
+    fx = _fixture("rmat24")
     w = graphgen.WORKLOADS["rmat24"]
     s, d, n = w.generate()
     g = tc.tc_build_csr(torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda(), n)
-    m = g.m
+    del s, d
+    assert g.m == int(fx["m"][0][0])
     lo, hi = tc.tc_edges(g)
-    lo = lo.cpu().numpy()
-    hi = hi.cpu().numpy()
-    T = tc.tc_count(g)
-    sup, T2 = tc.tc_edge_support(g)
-    sup = sup.cpu().numpy()
-    masks = {}
-    for k in w.truss_ks:
-        mk, left = tc.ktruss(g, k)
-        mk = mk.cpu().numpy()
-        assert int(mk.sum()) == left
-        masks[k] = mk
-    g.free()
-    del s, d
-
-    s, d, n = w.generate()
-    olo, ohi = oracle.canonical_edges(s, d, n)
-    del s, d
-    assert len(olo) == m
-    assert np.array_equal(lo, olo) and np.array_equal(hi, ohi)
+    assert [_sha(lo.cpu().numpy()), _sha(hi.cpu().numpy())] == fx["lo_hi_sha256"][0]
     del lo, hi
-    assert T == T2 and int(sup.sum(dtype=np.int64)) == 3 * T
-    og = oracle.OracleGraph(n, olo, ohi)
-    rng = np.random.default_rng(24)
-    sample = rng.integers(0, m, 3000)
-    assert np.array_equal(og.support_of(sample), sup[sample])
-    prev = None
-    for k in w.truss_ks:
-        mk = masks[k]
-        if prev is not None:
-            assert not (mk.astype(bool) & ~prev.astype(bool)).any()
-        prev = mk
-        inside = np.flatnonzero(mk)
-        outside = np.flatnonzero(mk == 0)
-        if len(inside):
-            si = rng.choice(inside, min(1500, len(inside)), replace=False)
-            assert (og.support_within_of(mk, si) >= k - 2).all(), k
-        if len(outside):
-            so = rng.choice(outside, min(1500, len(outside)), replace=False)
-            assert (og.support_within_of(mk, so) < k - 2).all(), k
+    T = tc.tc_count(g)
+    assert T == int(fx["triangles"][0][0])
+    sup, T2 = tc.tc_edge_support(g)
+    assert T2 == T
+    assert int(sup.sum(dtype=torch.int64)) == int(fx["support_sum"][0][0])
+    assert _sha(sup.cpu().numpy()) == fx["support_sha256"][0][0]
+    del sup
+    want = {int(k): (int(left), h) for k, left, h in fx["ktruss"]}
+    assert sorted(want) == list(w.truss_ks)
+    for k in w.truss_ks:                      # as the bench calls them
+        mask, c = tc.ktruss(g, k)
+        assert (c, _sha(mask.cpu().numpy().astype(np.int32))) == want[k], k
+    for mode in (2, 3):                       # intersections; bounded lists
+        prev = tc.tc_debug_peel_mode(mode)
+        try:
+            for k in (8, 4):                  # descending: each a fresh peel
+                mask, c = tc.ktruss(g, k)
+                assert (c, _sha(mask.cpu().numpy().astype(np.int32))) == want[k], (mode, k)
+        finally:
+            tc.tc_debug_peel_mode(prev)
+    g.free()
 
 
 def king_expected_support(lo, hi, M):

@@ -31,11 +31,13 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
 
 
-PEEL_MODES = {"lists": 1, "intersect": 2}
+PEEL_MODES = {"lists": 1, "intersect": 2, "hybrid": 3}
+PEEL_INFO = {"lists": 1, "intersect": 0, "hybrid": 2}   # tc_graph_info's peel_lists
 
 
 def gpu_all(src, dst, n, ks=(2, 3, 4, 5, 6)):
-    """Every ABI call on one graph; the peel runs in both of its forms."""
+    """Every ABI call on one graph; the peel runs in each of its forms (all
+    triangle lists, intersections, lists only below the support bound)."""
     g = tc.tc_build_csr(dev(src), dev(dst), n)
     lo, hi = tc.tc_edges(g)
     # the edge-per-warp kernel first, the thread-per-edge and the row
@@ -80,7 +82,7 @@ def gpu_all(src, dst, n, ks=(2, 3, 4, 5, 6)):
         finally:
             tc.tc_debug_peel_mode(prev)
         if g.m:
-            assert info["peel_lists"] == (1 if name == "lists" else 0)
+            assert info["peel_lists"] == PEEL_INFO[name], (name, info["peel_lists"])
         out["peel"][name] = dict(masks=masks, kmax=kmax, truss=truss.cpu().numpy())
     tc.tc_graph_free(g)
     return out
@@ -405,7 +407,9 @@ def test_resume_across_forms():
             tc.tc_debug_peel_mode(prev)
         assert c == want[k][2] and np.array_equal(mk.cpu().numpy(), want[k][0]), (k, mode)
 
-    L, X = PEEL_MODES["lists"], PEEL_MODES["intersect"]
+    L, X, H = PEEL_MODES["lists"], PEEL_MODES["intersect"], PEEL_MODES["hybrid"]
+    check_k(3, H)                             # hybrid, then full lists from its state
+    check_k(4, L)
     check_k(3, L)
     prev = tc.tc_debug_peel_mode(L)
     try:
@@ -418,6 +422,9 @@ def test_resume_across_forms():
     check_k(6, L)                             # list form from the intersection state
     check_k(4, L)                             # smaller k: fresh
     check_k(6, L)                             # resumes from k = 4
+    check_k(4, H)                             # hybrid fresh, then resumed by every form
+    check_k(5, H)
+    check_k(6, X)
     tc.tc_graph_free(g)
 
 
@@ -429,16 +436,18 @@ def test_every_intersection_kernel_builds_the_same_lists():
     og = oracle.OracleGraph.from_edges(src, dst, n)
     want_kmax, want_truss = og.truss_decomposition()
     for imode in (1, 2, 3, 4):
-        g = tc.tc_build_csr(dev(src), dev(dst), n)
-        pi = tc.tc_debug_intersect_mode(imode)
-        pp = tc.tc_debug_peel_mode(PEEL_MODES["lists"])
-        try:
-            kmax, truss = tc.ktruss_max(g)
-        finally:
-            tc.tc_debug_intersect_mode(pi)
-            tc.tc_debug_peel_mode(pp)
-        assert kmax == want_kmax and np.array_equal(truss.cpu().numpy(), want_truss), imode
-        tc.tc_graph_free(g)
+        for pmode in ("lists", "hybrid"):
+            g = tc.tc_build_csr(dev(src), dev(dst), n)
+            pi = tc.tc_debug_intersect_mode(imode)
+            pp = tc.tc_debug_peel_mode(PEEL_MODES[pmode])
+            try:
+                kmax, truss = tc.ktruss_max(g)
+            finally:
+                tc.tc_debug_intersect_mode(pi)
+                tc.tc_debug_peel_mode(pp)
+            assert kmax == want_kmax and np.array_equal(truss.cpu().numpy(), want_truss), \
+                (imode, pmode)
+            tc.tc_graph_free(g)
 
 
 def test_from_a_tab_separated_file(tmp_path):
