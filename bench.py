@@ -239,10 +239,13 @@ def run_step(tc, torch, src, dst, n, wl, stream, ev=None, outs=None, infos=None)
         for k in wl.truss_ks:
             mk_out = outs.get(f"mask{k}") if outs else None
             _, res[k] = tc.ktruss(g, k, out=mk_out, stream=stream)
-            if infos is not None:   # one peel launch per k
+            if infos is not None:   # one peel launch per k (the first also builds lists)
                 inf = tc.tc_graph_info(g)
                 infos.append({"peel_kernel_ns": inf["peel_kernel_ns"],
-                              "peel_bytes": inf["peel_bytes"]})
+                              "peel_bytes": inf["peel_bytes"],
+                              "lists_kernel_ns": inf["lists_kernel_ns"],
+                              "lists_bytes": inf["lists_bytes"],
+                              "peel_lists": inf["peel_lists"]})
         mark("truss")
     elif wl.name != "er4096":
         tr_out = outs.get("truss") if outs else None
@@ -271,15 +274,18 @@ def product_bytes(info, n, T):
     its row bounds and edge shift (24 B per vertex).  Other kernels: both
     out-lists of every oriented edge (4 B per entry, wedge_work entries),
     the row offsets (8 B per vertex) and the oriented edges' ids (4 B).
-    Support adds a 4-B write per edge; the list build the 8-B pair written
-    into each of the three lists of a triangle (24 B per triangle)."""
+    Support adds a 4-B write per edge.  A list build for every edge is made
+    by the row (or thread) kernel: its merge operands plus the 8-B pair
+    written into each of the three lists of a triangle (24 B per triangle);
+    a build made by the column kernel reports its own bytes (lists_bytes of
+    tc_graph_info), which the caller prefers."""
     m = info["m"]
     merge = 4 * info["wedge_work"] + 8 * (n + 1) + 4 * m
     if info.get("product_form") == 1:
         count = 4 * info["column_work"] + 28 * m + 24 * n
     else:
         count = merge
-    return count, count + 4 * m, count + 24 * T, merge
+    return count, count + 4 * m, merge + 24 * T, merge
 
 
 def kernel_rooflines(infos, count_bytes, support_bytes, lists_bytes, peak):
@@ -289,7 +295,8 @@ def kernel_rooflines(infos, count_bytes, support_bytes, lists_bytes, peak):
         for name, tkey, nbytes in (
                 ("masked product, count", "count_kernel_ns", count_bytes),
                 ("masked product, support", "support_kernel_ns", support_bytes),
-                ("triangle lists", "lists_kernel_ns", lists_bytes),
+                ("triangle lists", "lists_kernel_ns",
+                 inf["lists_bytes"] if (inf.get("lists_bytes") or -1) >= 0 else lists_bytes),
                 ("peel (k_peel)", "peel_kernel_ns", inf.get("peel_bytes"))):
             t = inf.get(tkey)
             if t is None or t <= 0:

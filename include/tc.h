@@ -203,6 +203,10 @@ typedef struct {
     int64_t product_form;  /* the masked-product kernel of the latest tc_count /
                               tc_edge_support launch: 1 columns, 2 warp per
                               edge, 3 thread per edge, 4 rows; 0 if none */
+    int64_t lists_bytes;   /* algorithmic bytes of the latest triangle-list build
+                              when the column kernel made it (4 per out-list
+                              word read, 24 per edge, 24 per vertex, 16 per
+                              list entry), else -1 */
 } tc_graph_info_t;
 
 /* Fills *info (host pointer) from values the library already holds; launches

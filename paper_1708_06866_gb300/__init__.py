@@ -137,7 +137,7 @@ class GraphInfo(ctypes.Structure):
                  "peel_rounds", "peel_lists", "count_kernel_ns", "support_kernel_ns",
                  "lists_kernel_ns", "peel_kernel_ns", "peel_bytes", "peel_scanned",
                  "peel_entries", "peel_searches", "peel_lookups", "peel_lowered",
-                 "truss_cached", "column_work", "product_form")]
+                 "truss_cached", "column_work", "product_form", "lists_bytes")]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

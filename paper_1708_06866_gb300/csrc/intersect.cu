@@ -427,8 +427,9 @@ __device__ __forceinline__ bool low_bit(const unsigned int* bits, int32_t e) {
     return (bits[e >> 5] >> (e & 31)) & 1u;
 }
 
-// One column's in-neighbours [i_first, i1) in steps of i_stride (32 per warp
-// of the group); returns the triangles found.  P: table position type.
+// One column's in-neighbours [i0, i1), in batches of 32 per warp; returns
+// the triangles found (LISTS: the 4-byte words of out-lists read instead).
+// P: table position type.
 template <int MODE, typename P>
 __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const int32_t* keys,
                                                        const P* pos, int log_cap, int32_t* cnt,
@@ -488,6 +489,7 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
                 for (int q = 0; q < TC_CX_UNROLL; ++q) {
                     const int64_t p = cb + 32 * q + lane;
                     w[q] = p < se ? a.col[p] : INT_MAX;
+                    if (MODE == LISTS) c += p < se;  // LISTS counts the entries read
                 }
                 // segments ascend: once a chunk starts above max N+(v), nothing later matches
                 if (__shfl_sync(0xffffffffu, w[0], 0) > vmax) break;
@@ -522,7 +524,7 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
                         }
                     }
                     if (h[q] >= 0) {
-                        ++c;
+                        if (MODE != LISTS) ++c;
                         if (MODE == SUPPORT) hit_support(h[q], p, so);
                     }
                 }
@@ -540,12 +542,13 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
                 int32_t w[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) w[q] = p + q < end ? a.col[p + q] : INT_MAX;
+                if (MODE == LISTS) c += (uint32_t)min((int64_t)4, end - p);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     if (w[q] > vmax) continue;
                     const int h = table_find(keys, log_cap, w[q]);
                     if (h < 0) continue;
-                    ++c;
+                    if (MODE != LISTS) ++c;
                     if (MODE == SUPPORT) hit_support(h, p + q, ou);
                     if (MODE == LISTS) {
                         const int iw = pos[h];
@@ -570,6 +573,7 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
             const unsigned int l1 = a.lowpos[end - ou];
             for (unsigned int q = a.lowpos[e_uv + 1]; q < l1; ++q) {
                 const int2 we = a.lowlist[q];  // {w, edge id of (u, w)}
+                acc += 2;                      // an 8-byte entry read
                 if (we.x > vmax) break;
                 const int h = table_find(keys, log_cap, we.x);
                 if (h < 0) continue;
@@ -1241,6 +1245,10 @@ int plan_triangle_lists(Graph* g, Scratch& sc, ListsPlan* lp) {
     }
     lp->form = concrete_form(g, 0);
     if (lp->form == 2) lp->form = 1;  // lists need a table kernel (the caller checked the size)
+    // every edge's list: the row kernel fills two of a triangle's three lists
+    // through its shared cursors (the column kernel only one), measured
+    // faster; lists below a bound: the column kernel, which skips segments
+    if (lp->form == 1 && lp->bound == 0 && intersect_mode() == 0) lp->form = 4;
     lp->thread = lp->form == 3;
     lp->blocks = product_blocks(g, lp->form, LISTS);
     TC_TRY(sc.alloc(&lp->partials, lp->blocks));
@@ -1288,6 +1296,10 @@ int enqueue_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off
                                   lp->bound, lp->lowbits, lp->lowpos, lp->lowlist));
     }
     TC_TRY(lp->timer.stop(s));
+    if (lp->form == 1) {  // the column kernel's words read, for its algorithmic bytes
+        k_reduce_partials<<<1, 1024, 0, s>>>(lp->partials, lp->blocks, g->dev_scalars + 7);
+        TC_LAUNCH_CHECK("k_reduce_partials");
+    }
     return TC_OK;
 }
 

@@ -908,6 +908,7 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
             TC_TRY(sc.alloc(&p.pairs, std::max<int64_t>(1, entries)));
         }
         p.lists.bound = p.bound;
+        p.lists.entries = entries;
         TC_TRY(plan_triangle_lists(g, sc, &p.lists));
         a.off = p.off;
         a.pairs = p.pairs;
@@ -1036,7 +1037,19 @@ int peel_finish(PeelPlan* pp, cudaStream_t s, int64_t* n_alive, int32_t* kmax) {
     Graph* g = p.g;
     PeelCtl& r = p.result;
     TC_CUDA_TRY(cudaMemcpyAsync(&r, p.a.ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, s));
+    const bool col_lists = p.tl && p.build_lists && p.lists.form == 1;
+    unsigned long long words = 0;
+    if (col_lists)
+        TC_CUDA_TRY(cudaMemcpyAsync(&words, g->dev_scalars + 7, sizeof(words),
+                                    cudaMemcpyDeviceToHost, s));
     TC_CUDA_TRY(cudaStreamSynchronize(s));
+    // column-kernel list build: the out-list words it read, per in-neighbour
+    // entry its id, edge id and the in-neighbour's row end and edge shift
+    // (24 B), per column its bounds and shift (24 B), per list entry the
+    // 8-byte pair and its 4-byte cursor read and written (16 B)
+    g->stats.lists_bytes = col_lists ? 4 * (int64_t)words + 24 * g->m + 24 * (int64_t)g->n +
+                                           16 * p.lists.entries
+                                     : -1;
     g->last_peel_rounds = r.rounds;
     g->stats.peel_ns = p.timer.elapsed_ns();
     g->stats.lists_ns = p.tl && p.build_lists ? p.lists.timer.elapsed_ns() : -1;

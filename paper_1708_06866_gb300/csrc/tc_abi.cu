@@ -371,6 +371,7 @@ int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream) {
     info->truss_cached = gg->truss_valid ? 1 : 0;
     info->column_work = gg->column_work;
     info->product_form = gg->stats.product_form;
+    info->lists_bytes = gg->stats.lists_bytes;
     return TC_OK;
 }
 

@@ -257,6 +257,7 @@ struct Graph {
     struct {
         int64_t count_ns = -1, support_ns = -1, lists_ns = -1, peel_ns = -1;
         int64_t product_form = 0;  // masked-product kernel of the latest count/support
+        int64_t lists_bytes = -1;  // algorithmic bytes of the latest column-kernel list build
         int64_t peel_bytes = -1;
         int64_t peel_scanned = 0, peel_entries = 0, peel_searches = 0, peel_lookups = 0,
                 peel_lowered = 0;
@@ -304,6 +305,7 @@ struct ListsPlan {
     bool thread = false;                 // built by the thread-per-edge kernel
     int form = 1;                        // the intersection kernel that builds them
     int32_t bound = 0;                   // lists only for edges of support < bound (0: all)
+    int64_t entries = 0;                 // pairs the lists hold
     int64_t low_edges = 0;               // ... edges with support in (0, bound)
     unsigned int* lowbits = nullptr;     // ... one bit per such edge
     unsigned int* lowpos = nullptr;      // ... their exclusive prefix count by edge id
