@@ -71,6 +71,8 @@ def _bind(lib):
     lib.oracle_truss_decomposition.restype = ctypes.c_int32
     lib.oracle_truss_components.argtypes = [vp, u8p, i32p, i32p]
     lib.oracle_truss_components.restype = ctypes.c_int64
+    lib.oracle_truss_levels.argtypes = [vp, ctypes.c_int32, i64p]
+    lib.oracle_truss_levels.restype = ctypes.c_int
     return lib
 
 
@@ -200,6 +202,14 @@ class OracleGraph:
         """Connected components of the k-truss (see components)."""
         mask, _, _ = self.ktruss(k)
         return self.components(mask)
+
+    def truss_levels(self, kmax: int):
+        """Sizes of the k-trusses for k = 3 .. kmax (the decomposition's first
+        levels, each continuing from the previous level's survivors)."""
+        sizes = np.zeros(max(int(kmax) - 2, 0), dtype=np.int64)
+        if self._lib.oracle_truss_levels(self._h, int(kmax), _ptr(sizes, ctypes.c_int64)) != 0:
+            raise ValueError("kmax < 3")
+        return [int(x) for x in sizes]
 
     def truss_decomposition(self):
         """(kmax, truss int32[m]): truss[e] = largest k whose k-truss holds e."""

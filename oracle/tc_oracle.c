@@ -367,6 +367,32 @@ int32_t oracle_truss_decomposition(const oracle_graph* g, int32_t* truss) {
     return kmax;
 }
 
+/* The first levels of the truss decomposition: k = 3 .. kmax, each level
+ * continuing from the previous level's survivors (Section III-B), stopping
+ * after kmax.  sizes[k - 3] = number of edges in the k-truss.  Returns 0, or
+ * -1 for kmax < 3. */
+int oracle_truss_levels(const oracle_graph* g, int32_t kmax, int64_t* sizes) {
+    if (kmax < 3) return -1;
+    const int64_t dmax = max_degree(g) + 1;
+    int32_t* s = (int32_t*)malloc(sizeof(int32_t) * (size_t)(g->m + 1));
+    uint8_t* alive = (uint8_t*)malloc((size_t)g->m + 1);
+    int64_t* queue = (int64_t*)malloc(sizeof(int64_t) * (size_t)(g->m + 1));
+    uint8_t* queued = (uint8_t*)calloc((size_t)g->m + 1, 1);
+    int64_t* pa = (int64_t*)malloc(sizeof(int64_t) * (size_t)dmax);
+    int64_t* pb = (int64_t*)malloc(sizeof(int64_t) * (size_t)dmax);
+    oracle_support(g, s);
+    memset(alive, 1, (size_t)g->m);
+    for (int32_t k = 3; k <= kmax; ++k)
+        sizes[k - 3] = peel_level(g, k, alive, s, NULL, queue, queued, pa, pb);
+    free(s);
+    free(alive);
+    free(queue);
+    free(queued);
+    free(pa);
+    free(pb);
+    return 0;
+}
+
 /* Connected components of the subgraph formed by the edges with alive[e] = 1
  * (the k-truss as a set of connected trusses, Section IV-A's enumeration of
  * k-trusses).  A component is the set of vertices reachable from one another

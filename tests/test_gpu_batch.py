@@ -105,3 +105,27 @@ def test_batch_count_only_and_errors():
     with pytest.raises(tc.TCError) as ei:
         tc.tc_batch_run(n, off, src, dst, k=1)
     assert ei.value.code == tc.TC_EINVAL
+
+
+def test_batch10k_sample_against_stored_oracle():
+    """The bench's batch (10,000 graphs, n log-uniform in [64, 65536], half
+    Erdős–Rényi and half R-MAT, seed 3) in one captured launch: a seeded
+    sample of 200 graphs covering every size class has the oracle's stored
+    edge count, triangle count and 4-truss size."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "batch10k_sample_oracle.txt")
+    rows = []
+    with open(path) as f:
+        for ln in f:
+            p = ln.split("#", 1)[0].split()
+            if p and p[0] == "g":
+                rows.append([int(x) for x in p[1:]])
+    assert len(rows) >= 200
+    n, off, src, dst, kind = graphgen.batch(10_000, seed=3)
+    out = tc.tc_batch_run(n, off, torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(),
+                          k=4, use_graph=True)
+    del src, dst
+    for i, nv, m, T, t4 in rows:
+        assert n[i] == nv
+        assert (out["edges"][i], out["triangles"][i], out["truss_edges"][i]) == (m, T, t4), i

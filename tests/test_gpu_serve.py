@@ -119,3 +119,55 @@ def test_server_degenerate_graphs_and_k2():
     srv.close()
     for _, r in trace:
         assert r.error is None and r.result == want[(r.graph, r.kind, r.k)], r
+
+
+def _stored_pool_answers():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "serve_pool_oracle.txt")
+    want = {}
+    with open(path) as f:
+        for ln in f:
+            p = ln.split("#", 1)[0].split()
+            if p and p[0] == "g":
+                gid, m, T = int(p[1]), int(p[3]), int(p[4])
+                want[(gid, "count", 0)] = T
+                for k, c in zip(range(3, 9), p[5:]):
+                    want[(gid, "ktruss", k)] = int(c)
+    return want
+
+
+def test_served_pool_matches_stored_oracle_with_results_not_kept():
+    """The bench's pool (64 R-MAT graphs, n log-uniform in [2^10, 2^22], seed
+    4) served concurrently with no results kept between requests (every
+    k-truss request peels): every graph's triangle count and k-truss sizes for
+    k = 3..8, in shuffled order, equal the oracle's stored answers."""
+    want = _stored_pool_answers()
+    pool = graphgen.rmat_pool(64, seed=4)
+    keys = sorted(want)
+    rng = np.random.default_rng(31)
+    order = rng.permutation(len(keys))
+    trace = [(0.0, serve.Request(i, *keys[j])) for i, j in enumerate(order)]
+    srv = serve.NativeServer(pool, slots=8, budget_bytes=120 << 30, keep_results=False)
+    srv.run(trace, open_loop=False)
+    st = srv.stats()
+    srv.close()
+    assert st["errors"] == 0 and st["max_concurrent"] >= 2
+    for _, r in trace:
+        assert r.error is None and r.result == want[(r.graph, r.kind, r.k)], r
+
+
+def test_results_alone_equal_results_in_the_mix_without_kept_results():
+    """With no results kept, concurrent requests (each k-truss request a
+    peel on the device, several at once on different streams) give what the
+    same queries give alone."""
+    pool = graphgen.rmat_pool(10, seed=17, n_min=1 << 8, n_max=1 << 14)
+    srv = serve.NativeServer(pool, slots=8, budget_bytes=8 << 30, keep_results=False)
+    trace = serve.poisson_trace(300, rate=0, graph_ids=list(pool), seed=18)
+    srv.run(trace, open_loop=False)
+    st = srv.stats()
+    srv.close()
+    assert st["errors"] == 0 and st["max_concurrent"] >= 2
+    alone = alone_results(pool)
+    for _, r in trace:
+        assert r.error is None and r.result == alone[(r.graph, r.kind, r.k)], r

@@ -367,6 +367,24 @@ def test_truss_decomposition_consistent_with_ktruss():
     assert g.ktruss(kmax + 1)[2] == 0 and g.ktruss(kmax)[2] > 0
 
 
+def test_truss_levels_equal_the_bulk_fixed_point_at_each_k():
+    """The decomposition's first levels (one support pass, then k = 3, 4, ...
+    each continuing from the previous survivors) give, at every k, the size
+    of the k-truss found by an independent bulk fixed point on the whole
+    graph (the k-trusses nest, Section III-B); K_n: every edge up to k = n,
+    nothing above."""
+    for n, lo, hi in small_random_graphs(30, 14, seed=6):
+        g = oracle.OracleGraph(n, lo, hi)
+        sizes = g.truss_levels(7)
+        want = [int(bulk_fixed_point_truss(n, lo, hi, k).sum()) for k in range(3, 8)]
+        assert sizes == want, (n, sizes, want)
+    s, d, n = graphgen.complete(9)
+    g = oracle.OracleGraph.from_edges(s, d, n)
+    assert g.truss_levels(11) == [36] * 7 + [0, 0]
+    with pytest.raises(ValueError):
+        g.truss_levels(2)
+
+
 def test_support_invariant_on_rmat():
     s, d, n = graphgen.rmat(12, seed=1)
     g = oracle.OracleGraph.from_edges(s, d, n)
