@@ -289,6 +289,11 @@ WORKLOADS = {
         "rmat18", "rmat", n=1 << 18, scale=18, seed=1,
         description="R-MAT scale 18, edgefactor 16, permuted; count + support + full truss "
                     "decomposition (the small case for hardware-counter captures)"),
+    "rmat22": Workload(
+        "rmat22", "rmat", n=1 << 22, scale=22, seed=1, truss_ks=(3, 4, 6, 8),
+        description="R-MAT scale 22, edgefactor 16, permuted; count + support + k-truss at "
+                    "k=3,4,6,8 (3T >= 2^32, so the scale-24 path at a quarter of its size: the "
+                    "small case for hardware-counter captures of that path)"),
     "king8192": Workload(
         "king8192", "king", n=8192 * 8192, scale=8192, seed=0,
         description="the 8192 x 8192 8-neighbour image graph (Section IV-C, Table II's family): "

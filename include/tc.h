@@ -126,6 +126,18 @@ int tc_edge_support(tc_graph* g, int32_t* support_out, int64_t* triangles_out,
 int ktruss(tc_graph* g, int32_t k, uint8_t* mask_out, int64_t* edges_out, void* cuda_stream);
 
 /*
+ * ktruss_sizes — the number of edges in the k-truss for every k in
+ * [k_lo, k_hi] (Section III-B: the k-trusses nest, so the decomposition's
+ * levels k_lo, k_lo + 1, ... each peel the previous level's survivors; one
+ * peel from the supports answers the whole range, stopping after k_hi).
+ * sizes_out: host int64, k_hi - k_lo + 1 entries (sizes_out[i] for
+ * k = k_lo + i; k = 2 gives every edge).  Uses the kept truss numbers of an
+ * earlier ktruss_max when the graph keeps results.  Synchronises the stream.
+ * Errors: TC_EINVAL unless 2 <= k_lo <= k_hi < k_lo + 64.
+ */
+int ktruss_sizes(tc_graph* g, int32_t k_lo, int32_t k_hi, int64_t* sizes_out, void* cuda_stream);
+
+/*
  * ktruss_max — truss decomposition (Section III-B): k = 3, 4, ... each level
  * peeling the previous level's survivors, until none is left.
  * kmax_out: host int32, the largest k with a non-empty k-truss (2 if the
@@ -217,6 +229,19 @@ int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream);
  * of |N+(u)| + |N+(v)| into *out (host), and with it tc_graph_info's
  * column_work.  Synchronises the stream. */
 int tc_graph_wedge_work(tc_graph* g, int64_t* out, void* cuda_stream);
+
+/*
+ * Chooses whether the graph keeps results between calls (keep != 0, the
+ * default): the truss numbers of its latest ktruss_max (later ktruss calls
+ * then threshold them, Section III-B: the k-trusses nest) and the state of
+ * its latest ktruss (a later call with a k at least as large resumes from
+ * that truss).  With keep = 0 every ktruss and ktruss_max call peels from
+ * the supports, and what was kept is released; structures (the CSR, the
+ * supports, triangle lists) are still kept within the memory bound.
+ * Results are the same either way; a serving loop that must do each
+ * request's work turns it off.  Errors: TC_EINVAL for a NULL graph.
+ */
+int tc_graph_set_result_cache(tc_graph* g, int32_t keep);
 
 /*
  * Bounds the optional device memory the library may keep for this graph
@@ -345,6 +370,14 @@ int tc_server_create(const tc_graph_source* sources, int32_t num_graphs, int64_t
 int tc_server_run(tc_server* srv, const tc_request* reqs, int64_t num_reqs, int32_t open_loop,
                   int32_t slots, tc_response* out, double* wall_s);
 
+/* Whether the server's graphs keep results between requests (keep != 0,
+ * the default: a graph's first k-truss request computes and keeps its truss
+ * decomposition, later ones threshold it).  keep = 0: every k-truss request
+ * peels on the device (tc_graph_set_result_cache on each graph, now and on
+ * those built later); the CSR, supports and structures within the memory
+ * bound stay resident.  Call between runs.  Errors: TC_EINVAL for NULL. */
+int tc_server_set_result_cache(tc_server* srv, int32_t keep);
+
 /* Counters of the server's life so far (host struct).  Launches nothing. */
 int tc_server_get_stats(const tc_server* srv, tc_server_stats* out);
 
@@ -381,13 +414,16 @@ typedef struct {
     int64_t query_ns;          /* supports + per-graph sums + peel */
     int64_t m;                 /* edges of all graphs after cleaning */
     int64_t triangles;         /* triangles of all graphs */
-    int32_t intersect_form;    /* 1 = row/hash kernel, 2 = edge-per-warp kernel,
-                                  3 = edge-per-thread kernel */
-    int32_t peel_form;         /* 0 = no peel, 1 = triangle lists, 2 = intersections */
+    int32_t intersect_form;    /* 1 = column kernel, 2 = edge-per-warp kernel,
+                                  3 = edge-per-thread kernel, 4 = row kernel */
+    int32_t peel_form;         /* 0 = no peel, 1 = triangle lists, 2 = intersections
+                                  (or lists below the support bound with them) */
     int32_t tuned_from_cache;  /* 1 if the kernel choice came from the tuner's cache */
     int32_t captured;          /* 1 if the query ran as one CUDA graph launch */
     int32_t peel_blocks;       /* the tuner's cap on the peel's grid (0 = none) */
-    int32_t pad;
+    int32_t light_degree;      /* column kernel: the tuner's degree bound of the
+                                  columns that take a warp each (heavier ones take
+                                  a block); 0 for the other kernels */
 } tc_batch_stats_t;
 
 typedef struct {

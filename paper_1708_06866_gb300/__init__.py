@@ -28,9 +28,11 @@ from . import _build
 
 __all__ = [
     "TCError", "Graph", "load_library", "library_path", "tc_build_csr", "tc_count",
-    "tc_edge_support", "ktruss", "ktruss_max", "ktruss_components", "tc_num_edges", "tc_num_vertices", "tc_edges",
+    "tc_edge_support", "ktruss", "ktruss_sizes", "ktruss_max", "ktruss_components", "tc_num_edges",
+    "tc_num_vertices", "tc_edges",
     "tc_graph_info", "tc_graph_wedge_work", "tc_launch_count", "tc_batch_run",
-    "tc_graph_set_memory_limit", "tc_read_edges", "tc_debug_server_fake", "GraphSource",
+    "tc_graph_set_memory_limit", "tc_graph_set_result_cache", "tc_read_edges",
+    "tc_debug_server_fake", "GraphSource",
     "ServeRequest", "ServeResponse", "ServerStats", "TC_REQ_COUNT", "TC_REQ_KTRUSS",
     "tc_graph_free", "tc_strerror", "tc_last_error", "tc_debug_fail_alloc",
     "tc_debug_spin_limit_ns", "tc_debug_peel_mode", "tc_debug_intersect_mode", "TC_OK", "TC_EINVAL", "TC_ERANGE", "TC_ENOMEM", "TC_ECUDA",
@@ -76,6 +78,9 @@ def load_library(build_if_missing: bool = True):
             "tc_graph_info": (ctypes.c_int, [vp, ctypes.POINTER(GraphInfo), vp]),
             "tc_launch_count": (i64, []),
             "tc_graph_set_memory_limit": (ctypes.c_int, [vp, i64]),
+            "tc_graph_set_result_cache": (ctypes.c_int, [vp, i32]),
+            "ktruss_sizes": (ctypes.c_int, [vp, i32, i32, ctypes.POINTER(i64), vp]),
+            "tc_server_set_result_cache": (ctypes.c_int, [vp, i32]),
             "ktruss_components": (ctypes.c_int, [vp, i32, vp, vp, ctypes.POINTER(i64), vp]),
             "tc_read_edges": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, vp, vp, i64,
                                              ctypes.POINTER(i64), ctypes.POINTER(i32)]),
@@ -149,7 +154,7 @@ class BatchStats(ctypes.Structure):
                 ("m", ctypes.c_int64), ("triangles", ctypes.c_int64),
                 ("intersect_form", ctypes.c_int32), ("peel_form", ctypes.c_int32),
                 ("tuned_from_cache", ctypes.c_int32), ("captured", ctypes.c_int32),
-                ("peel_blocks", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("peel_blocks", ctypes.c_int32), ("light_degree", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -327,6 +332,15 @@ def ktruss_components(g: Graph, k: int, stream=None, vertices: bool = True):
     return el, vl, c.value
 
 
+def ktruss_sizes(g: Graph, k_lo: int, k_hi: int, stream=None):
+    """Sizes of the k-trusses for k = k_lo .. k_hi (one peel for the range)."""
+    nk = int(k_hi) - int(k_lo) + 1
+    out = (ctypes.c_int64 * max(nk, 1))()
+    _check(load_library().ktruss_sizes(g.handle, int(k_lo), int(k_hi), out,
+                                       _stream_handle(stream)), "ktruss_sizes")
+    return [int(out[i]) for i in range(nk)]
+
+
 def ktruss_max(g: Graph, out=None, stream=None, want_truss: bool = True):
     """Truss decomposition: (kmax, per-edge truss numbers or None)."""
     torch = _torch()
@@ -372,6 +386,12 @@ def tc_graph_wedge_work(g: Graph, stream=None) -> int:
     _check(load_library().tc_graph_wedge_work(g.handle, ctypes.byref(out), _stream_handle(stream)),
            "tc_graph_wedge_work")
     return out.value
+
+
+def tc_graph_set_result_cache(g: Graph, keep: bool):
+    """Whether the graph keeps results (truss numbers, the latest k-truss) between calls."""
+    _check(load_library().tc_graph_set_result_cache(g.handle, 1 if keep else 0),
+           "tc_graph_set_result_cache")
 
 
 def tc_graph_set_memory_limit(g: Graph, nbytes: int):

@@ -91,7 +91,8 @@ __global__ void k_segment_sums(const T* __restrict__ x, const int64_t* __restric
 }
 
 struct Choice {
-    int intersect = 1;    // 1 row/hash kernel, 2 edge-per-warp, 3 edge-per-thread
+    int intersect = 1;    // 1 columns, 2 edge-per-warp, 3 edge-per-thread, 4 rows
+    int light = LIGHT_DEG;  // columns: the degree bound of warp-per-column (light) columns
     int peel = PEEL_AUTO;
     int peel_blocks = 0;  // cap on the peel's grid (0 = its own rule)
 };
@@ -111,21 +112,30 @@ unsigned grid_items(int64_t n, int per = 256) {
 // Times each candidate on the batch itself and keeps the fastest.  The
 // peel candidates must agree on the number of surviving edges.
 int autotune(Graph* g, int32_t k, Choice* c, cudaStream_t s) {
-    // masked-product kernel
+    // masked-product kernel and, for the column kernel, the degree bucket
+    // boundary: columns up to `light` take a warp each, heavier ones a block
+    struct Cand {
+        int form, light;
+    };
+    const Cand cands[] = {{1, 32}, {1, 64}, {1, LIGHT_DEG}, {4, 0}, {2, 0}, {3, 0}};
     int64_t best_ns = -1;
-    for (int form : {1, 2, 3}) {
-        if (form == 1 && !triangle_lists_supported(g)) continue;  // the row kernel's limit
-        if (form == 3 && g->max_out > 64) continue;  // merges grow with the out-lists
+    for (const Cand& cd : cands) {
+        if ((cd.form == 1 || cd.form == 4) && !triangle_lists_supported(g)) continue;  // table size
+        if (cd.form == 1 && cd.light > LIGHT_DEG) continue;
+        if (cd.form == 3 && g->max_out > 64) continue;  // merges grow with the out-lists
+        g->col_light_deg = cd.form == 1 ? cd.light : LIGHT_DEG;
         int64_t T = 0;
-        TC_TRY(compute_support(g, g->support, true, &T, s, form));
+        TC_TRY(compute_support(g, g->support, true, &T, s, cd.form));
         g->triangles = T;
         g->support_valid = true;
         const int64_t ns = g->stats.support_ns;
         if (best_ns < 0 || (ns >= 0 && ns < best_ns)) {
             best_ns = ns;
-            c->intersect = form;
+            c->intersect = cd.form;
+            c->light = cd.form == 1 ? cd.light : LIGHT_DEG;
         }
     }
+    g->col_light_deg = c->light;
     if (k < 2) return TC_OK;
     // peel form
     best_ns = -1;
@@ -291,6 +301,7 @@ int batch_run(const tc_batch_desc* d, cudaStream_t user_stream) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune[sig] = choice;
     } else if (g.m > 0) {
+        g.col_light_deg = choice.light;
         if (d->k >= 2 && choice.peel != PEEL_INTERSECT) {
             // the triangle-list form is sized by T: count before planning
             int64_t T = 0;
@@ -397,6 +408,7 @@ int batch_run(const tc_batch_desc* d, cudaStream_t user_stream) {
         st->intersect_form = choice.intersect;
         st->peel_form = peel ? (peel_uses_lists(plan) ? 1 : 2) : 0;
         st->peel_blocks = peel ? choice.peel_blocks : 0;
+        st->light_degree = choice.intersect == 1 ? choice.light : 0;
         st->tuned_from_cache = cached ? 1 : 0;
         st->captured = d->use_graph ? 1 : 0;
     }

@@ -216,29 +216,56 @@ __global__ void k_upper(const uint64_t* __restrict__ keys, int64_t nnz, int bits
     }
 }
 
-// [0] = largest degree, [1] = largest out-list, [2] = rows of degree at
-// most LIGHT_DEG (rows ascend by degree, so these are the rows below that
-// count: the column kernel's light columns).
+// The column kernel's layout of the out-lists by edge id, from the sorted
+// (row, neighbour) keys of the symmetric CSR: an out-entry (neighbour above
+// the row) at position p is edge p - oshift[row], whose head is the
+// neighbour; an in-entry (neighbour u below the row v) is the
+// (p - first edge id of v)-th in-entry overall, and gets u's out-edge end,
+// rowptr[u + 1] - oshift[u].
+__global__ void k_col_aux(const uint64_t* __restrict__ keys, int64_t nnz, int bits,
+                          const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
+                          const int64_t* __restrict__ oshift, int32_t* __restrict__ head,
+                          int32_t* __restrict__ iend) {
+    const uint64_t mask = (1ull << bits) - 1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
+        const uint64_t k = keys[p];
+        const int32_t r = (int32_t)(k >> bits), c = (int32_t)(k & mask);
+        if (c > r) {
+            head[p - oshift[r]] = c;
+        } else {
+            const int64_t first = upper[r] - oshift[r];  // edge id of r's first out-entry
+            iend[p - first] = (int32_t)(rowptr[c + 1] - oshift[c]);
+        }
+    }
+}
+
+// [0] = largest degree, [1] = largest out-list, [2 + i] = rows of degree
+// at most 16 << i, i < 4 (rows ascend by degree, so these are the rows below
+// that count: the column kernel's light columns for that bound).
 __global__ void k_row_stats(const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
                             int32_t n, unsigned long long* __restrict__ out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    unsigned long long md = 0, mo = 0, nl = 0;
+    unsigned long long md = 0, mo = 0, nl[4] = {0, 0, 0, 0};
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
         const int64_t d = rowptr[r + 1] - rowptr[r];
         md = max(md, (unsigned long long)d);
         mo = max(mo, (unsigned long long)(rowptr[r + 1] - upper[r]));
-        nl += d <= LIGHT_DEG;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) nl[i] += d <= (16 << i);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         md = max(md, __shfl_xor_sync(0xffffffffu, md, o));
         mo = max(mo, __shfl_xor_sync(0xffffffffu, mo, o));
-        nl += __shfl_xor_sync(0xffffffffu, nl, o);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) nl[i] += __shfl_xor_sync(0xffffffffu, nl[i], o);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicMax(&out[0], md);
         atomicMax(&out[1], mo);
-        atomicAdd(&out[2], nl);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) atomicAdd(&out[2 + i], nl[i]);
     }
 }
 
@@ -420,15 +447,22 @@ int build_graph(Graph* g, const int32_t* src, const int32_t* dst, cudaStream_t s
             k_oshift<<<grid_for(n), 256, 0, s>>>(g->upper, obase, n, g->oshift);
             TC_LAUNCH_CHECK("k_oshift");
         }
-        TC_CUDA_TRY(cudaMemsetAsync(g->dev_scalars, 0, 3 * sizeof(unsigned long long), s));
+        TC_TRY(dev_alloc_n(&g->head, m, s));
+        TC_TRY(dev_alloc_n(&g->iend, m, s));
+        if (m > 0) {
+            k_col_aux<<<grid_for(nnz), 256, 0, s>>>(pkeys, nnz, bits, g->rowptr, g->upper,
+                                                    g->oshift, g->head, g->iend);
+            TC_LAUNCH_CHECK("k_col_aux");
+        }
+        TC_CUDA_TRY(cudaMemsetAsync(g->dev_scalars, 0, 6 * sizeof(unsigned long long), s));
         k_row_stats<<<grid_for(n), 256, 0, s>>>(g->rowptr, g->upper, n, g->dev_scalars);
         TC_LAUNCH_CHECK("k_row_stats");
-        unsigned long long st[3];
+        unsigned long long st[6];
         TC_CUDA_TRY(cudaMemcpyAsync(st, g->dev_scalars, sizeof(st), cudaMemcpyDeviceToHost, s));
         TC_CUDA_TRY(cudaStreamSynchronize(s));
         g->max_deg = (int32_t)st[0];
         g->max_out = (int32_t)st[1];
-        g->light_rows = (int32_t)st[2];
+        for (int i = 0; i < 4; ++i) g->light_rows[i] = (int32_t)st[2 + i];
         TC_TRY(check_dev_err(g->dev_err, s));
     }
     return TC_OK;

@@ -365,14 +365,17 @@ __global__ void __launch_bounds__(IX_THREADS) k_edges_warp(
 // Columns of vertices of degree > LIGHT_DEG (the highest ranks) get one block
 // each, its warps sharing the in-neighbours; the rest (most of the vertices)
 // get one warp each with a warp-private table, so light columns pay no block
-// barrier.  In-neighbour u's segment of N+(u) starts after v's own entry,
-// at position eid(u, v) + oshift[u]; segments longer than CX_SHORT are
-// streamed by the whole warp (coalesced, CX_UNROLL chunks in flight),
-// shorter ones by one lane each.
+// barrier.  The out-lists are read by edge id (head[e] = the higher end of
+// edge e; a row's out-edges have consecutive ids), so in-neighbour u's
+// segment of N+(u) after v is head[eid(u, v) + 1 .. iend), iend (the end of
+// u's out-edge ids) stored with the in-entry by the build: both come from
+// coalesced loads, with no per-neighbour lookups.  Segments longer than
+// CX_SHORT are streamed by the whole warp (coalesced, CX_UNROLL chunks in
+// flight), shorter ones by one lane each.
 //
-// Credits of a triangle (u, v, w) found at N+(u) position p, table slot h:
-// (v, w) is the column's own edge (position pos[h] of N+(v)): a shared
-// counter, flushed once per column; (u, w) is edge p - oshift[u]: a global
+// Credits of a triangle (u, v, w) found at edge id q of u's out-edges, table
+// slot h: (v, w) is the column's own edge (position pos[h] of N+(v)): a
+// shared counter, flushed once per column; (u, w) is edge q: a global
 // atomic; (u, v): one add per segment.  LISTS writes the pair into the three
 // lists: (v, w) from the bottom through the column's shared cursors (its
 // bottom entries come only from this column), (u, v) and (u, w) from the top
@@ -403,8 +406,9 @@ constexpr int CX_LIGHT_CAP = 1 << CX_LIGHT_LOG_CAP;
 struct ColArgs {
     const int64_t* rowptr;
     const int64_t* upper;
-    const int32_t* col;
+    const int32_t* head;   // head[e]: the higher end of edge e
     const int32_t* eid;
+    const int32_t* iend;   // per in-entry: end of its neighbour's out-edge ids
     const int64_t* oshift;
     int32_t n;
     int32_t n_light;   // ranks [0, n_light) are light columns
@@ -440,27 +444,32 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
     const int lane = threadIdx.x & 31;
     const bool partial = MODE == LISTS && a.bound > 0;
     unsigned long long acc = 0;
-    // batches of 32 in-neighbours: handed out by the shared counter (a
-    // block's warps sharing a column take them as they finish), or all to
-    // this warp
+    // batches of in-neighbours: handed out by the shared counter (a block's
+    // warps sharing a column take them as they finish), or all to this warp.
+    // A shared column with few in-neighbours uses smaller batches (down to
+    // 4, about two per warp) so that every warp gets some; lanes past the
+    // batch take none, long segments are still streamed by the whole warp.
+    int bsz = 32;
+    if (next) {
+        const int64_t want = (i1 - i0 + 2 * RX_WARPS - 1) / (2 * RX_WARPS);
+        bsz = (int)max((int64_t)4, min((int64_t)32, want));
+    }
     auto take = [&](int64_t done) -> int64_t {
         if (!next) return done;  // static: i0, i0 + stride, ...
         unsigned b = 0;
-        if (lane == 0) b = atomicAdd(next, 32u);
+        if (lane == 0) b = atomicAdd(next, (unsigned)bsz);
         return i0 + (int64_t)__shfl_sync(0xffffffffu, b, 0);
     };
     for (int64_t ib = take(i0); ib < i1; ib = take(ib + stride)) {
-        const int64_t i = ib + lane;
-        int64_t s = 0, end = 0, ou = 0;
-        int32_t e_uv = 0, u = 0;
+        const int64_t i = lane < bsz ? ib + lane : i1;  // lanes past the batch: none
+        int64_t s = 0, end = 0;
+        int32_t e_uv = 0;
         bool luv = true;   // (u, v) has a list
         bool full = true;  // the whole segment is streamed
         if (i < i1) {
-            u = a.col[i];
             e_uv = a.eid[i];
-            ou = a.oshift[u];
-            s = (int64_t)e_uv + ou + 1;  // N+(u) entries after v
-            end = a.rowptr[u + 1];
+            s = (int64_t)e_uv + 1;        // u's out-edges after (u, v), by edge id
+            end = a.iend[i - ev];         // in-entries of column v start at index rowptr[v] - ev
             if (partial) {
                 luv = low_bit(a.lowbits, e_uv);
                 full = luv || col_low;
@@ -468,9 +477,10 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
         }
         const int64_t len = full ? end - s : 0;
         // a triangle (u, v, w) found at N+(u) position p, slot h
-        auto hit_support = [&](int h, int64_t p, int64_t o) {
+        // a triangle (u, v, w): w at edge id q of u's out-edges, table slot h
+        auto hit_support = [&](int h, int64_t q) {
             atomicAdd(&cnt[pos[h]], 1);
-            atomicAdd(&a.sup[p - o], 1);
+            atomicAdd(&a.sup[q], 1);
         };
         // long segments: the whole warp, one after another
         unsigned lng = __ballot_sync(0xffffffffu, len > TC_CX_SHORT);
@@ -479,7 +489,6 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
             lng &= lng - 1;
             const int64_t ss = __shfl_sync(0xffffffffu, s, src);
             const int64_t se = __shfl_sync(0xffffffffu, end, src);
-            const int64_t so = __shfl_sync(0xffffffffu, ou, src);
             const int32_t suv = __shfl_sync(0xffffffffu, e_uv, src);
             const bool sluv = __shfl_sync(0xffffffffu, luv, src);
             uint32_t c = 0;
@@ -488,7 +497,7 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
 #pragma unroll
                 for (int q = 0; q < TC_CX_UNROLL; ++q) {
                     const int64_t p = cb + 32 * q + lane;
-                    w[q] = p < se ? a.col[p] : INT_MAX;
+                    w[q] = p < se ? a.head[p] : INT_MAX;
                     if (MODE == LISTS) c += p < se;  // LISTS counts the entries read
                 }
                 // segments ascend: once a chunk starts above max N+(v), nothing later matches
@@ -511,7 +520,7 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
                             base = __shfl_sync(0xffffffffu, base, ldr) - (unsigned)__popc(msk);
                             if (h[q] >= 0) {
                                 const int iw = pos[h[q]];
-                                const int32_t e_vw = (int32_t)(ev + iw), e_uw = (int32_t)(p - so);
+                                const int32_t e_vw = (int32_t)(ev + iw), e_uw = (int32_t)p;
                                 if (sluv)
                                     a.pairs[base + __popc(msk & lanemask_lt())] =
                                         make_int2(e_uw, e_vw);
@@ -525,7 +534,7 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
                     }
                     if (h[q] >= 0) {
                         if (MODE != LISTS) ++c;
-                        if (MODE == SUPPORT) hit_support(h[q], p, so);
+                        if (MODE == SUPPORT) hit_support(h[q], p);
                     }
                 }
             }
@@ -541,7 +550,7 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
             for (int64_t p = s; p < end; p += 4) {
                 int32_t w[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) w[q] = p + q < end ? a.col[p + q] : INT_MAX;
+                for (int q = 0; q < 4; ++q) w[q] = p + q < end ? a.head[p + q] : INT_MAX;
                 if (MODE == LISTS) c += (uint32_t)min((int64_t)4, end - p);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -549,10 +558,10 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
                     const int h = table_find(keys, log_cap, w[q]);
                     if (h < 0) continue;
                     if (MODE != LISTS) ++c;
-                    if (MODE == SUPPORT) hit_support(h, p + q, ou);
+                    if (MODE == SUPPORT) hit_support(h, p + q);
                     if (MODE == LISTS) {
                         const int iw = pos[h];
-                        const int32_t e_vw = (int32_t)(ev + iw), e_uw = (int32_t)(p + q - ou);
+                        const int32_t e_vw = (int32_t)(ev + iw), e_uw = (int32_t)(p + q);
                         if (luv) a.pairs[atomicSub(&a.top[e_uv], 1u) - 1u] = make_int2(e_uw, e_vw);
                         if (!partial || low_bit(a.lowbits, e_uw))
                             a.pairs[atomicSub(&a.top[e_uw], 1u) - 1u] = make_int2(e_uv, e_vw);
@@ -569,8 +578,8 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
         // lists below a bound, segment not streamed: only u's low out-entries
         // above v can close a triangle that needs an entry, in the (u, w) list
         if (partial && i < i1 && !full && s < end) {
-            // u's low out-entries after v: edge ids e_uv + 1 .. (end - ou) - 1
-            const unsigned int l1 = a.lowpos[end - ou];
+            // u's low out-entries after v: edge ids e_uv + 1 .. end - 1
+            const unsigned int l1 = a.lowpos[end];
             for (unsigned int q = a.lowpos[e_uv + 1]; q < l1; ++q) {
                 const int2 we = a.lowlist[q];  // {w, edge id of (u, w)}
                 acc += 2;                      // an 8-byte entry read
@@ -615,7 +624,7 @@ __global__ void __launch_bounds__(RX_THREADS, TC_CX_MIN_BLOCKS) k_cols(ColArgs a
             const int64_t i0 = a.rowptr[v], b0 = a.upper[v], b1 = a.rowptr[v + 1];
             const int dv = (int)(b1 - b0);
             if (dv < 1 || b0 == i0) continue;  // no out-list or no in-neighbour: no triangle
-            const int64_t ev = b0 - (MODE == COUNT ? 0 : a.oshift[v]);
+            const int64_t ev = b0 - a.oshift[v];  // first out-edge id of v
             const int log_cap = min(table_log_cap(dv), a.max_log_cap);
             const int cap = 1 << log_cap;
             for (int i = threadIdx.x; i < cap; i += RX_THREADS) keys[i] = -1;
@@ -631,13 +640,13 @@ __global__ void __launch_bounds__(RX_THREADS, TC_CX_MIN_BLOCKS) k_cols(ColArgs a
                 }
             const bool col_low = __syncthreads_or(low) != 0;
             for (int i = threadIdx.x; i < dv; i += RX_THREADS) {
-                const int32_t w = a.col[b0 + i];
+                const int32_t w = a.head[ev + i];
                 uint32_t h = slot_of(w, log_cap);
                 while (atomicCAS(&keys[h], -1, w) != -1) h = (h + 1) & (cap - 1);
                 pos[h] = (uint16_t)i;
             }
             __syncthreads();
-            const int32_t vmax = a.col[b1 - 1];
+            const int32_t vmax = a.head[ev + dv - 1];
             if (TC_CX_DYNAMIC)
                 acc += col_walk<MODE>(a, keys, pos, log_cap, cnt, sbase, ev, vmax, col_low, i0, b0,
                                       &s_next);
@@ -678,7 +687,7 @@ __global__ void __launch_bounds__(RX_THREADS, TC_CX_MIN_BLOCKS) k_cols(ColArgs a
                     if (lane == 0) atomicOr(a.err, DEV_ERR_BOUNDS);
                     continue;
                 }
-                const int64_t ev = b0 - (MODE == COUNT ? 0 : a.oshift[v]);
+                const int64_t ev = b0 - a.oshift[v];  // first out-edge id of v
                 for (int i = lane; i < CX_LIGHT_CAP; i += 32) keys[i] = -1;
                 bool low = false;
                 if (MODE != COUNT)
@@ -693,13 +702,13 @@ __global__ void __launch_bounds__(RX_THREADS, TC_CX_MIN_BLOCKS) k_cols(ColArgs a
                 const bool col_low = __any_sync(0xffffffffu, low);
                 __syncwarp();
                 for (int i = lane; i < dv; i += 32) {
-                    const int32_t w = a.col[b0 + i];
+                    const int32_t w = a.head[ev + i];
                     uint32_t h = slot_of(w, CX_LIGHT_LOG_CAP);
                     while (atomicCAS(&keys[h], -1, w) != -1) h = (h + 1) & (CX_LIGHT_CAP - 1);
                     pos[h] = (uint8_t)i;
                 }
                 __syncwarp();
-                const int32_t vmax = a.col[b1 - 1];
+                const int32_t vmax = a.head[ev + dv - 1];
                 acc += col_walk<MODE>(a, keys, pos, CX_LIGHT_LOG_CAP, cnt, sbase, ev, vmax, col_low,
                                       i0, b0, nullptr, 32);
                 __syncwarp();
@@ -1038,8 +1047,12 @@ int launch_cols(Graph* g, int32_t* sup, const unsigned long long* off, unsigned 
     const size_t sm = cols_smem(lc, MODE, max_pos);
     unsigned int* next = reinterpret_cast<unsigned int*>(g->dev_scalars + 5);
     TC_CUDA_TRY(cudaMemsetAsync(next, 0, 2 * sizeof(unsigned int), s));
-    ColArgs a{g->rowptr, g->upper, g->col, g->eid, g->oshift, g->n, g->light_rows, sup, off, top,
-              pairs, next, partials, lc, max_pos, g->dev_err, bound, lowbits, lowpos, lowlist};
+    // light columns: degree <= the graph's bound (16, 32, 64 or LIGHT_DEG)
+    int li = 3;
+    while (li > 0 && (16 << li) > g->col_light_deg) --li;
+    ColArgs a{g->rowptr, g->upper, g->head, g->eid, g->iend, g->oshift, g->n, g->light_rows[li], sup,
+              off, top, pairs, next, partials, lc, max_pos, g->dev_err, bound, lowbits, lowpos,
+              lowlist};
     k_cols<MODE><<<blocks, RX_THREADS, sm, s>>>(a);
     TC_LAUNCH_CHECK("k_cols");
     return TC_OK;

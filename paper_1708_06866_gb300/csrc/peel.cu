@@ -114,6 +114,9 @@ struct PeelArgs {
     int32_t k_first;
     int32_t r_first;  // first round number (2 when resuming: state -1 = removed before)
     int32_t single;  // 1: peel level k_first only
+    int32_t no_compact;  // 1: col / eid are the graph's own (read only): never compact
+    int32_t k_last;      // decomposition: stop after level k_last (0: until empty)
+    long long* level_left;  // ... and record the k-truss size of levels k_first..k_last
     int64_t spin_ns;
 };
 
@@ -654,7 +657,7 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
             fi ^= 1;
             ++r;
             // compact the rows once half of their entries are removed edges
-            if (IX && 4 * n_alive < nnz) {
+            if (IX && !a.no_compact && 4 * n_alive < nnz) {
                 ++compactions;
                 const Round now{r};
                 for (int64_t row = gwarp; row < a.n; row += nwarps) {
@@ -695,7 +698,11 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
         // round r's frontier was empty; the next scan takes a fresh round number
         ++r;
         if (a.single) break;
+        if (leader && a.level_left)  // levels up to k_next - 1 remove nothing more
+            for (int32_t kk = k; kk < k_next && kk <= a.k_last; ++kk)
+                a.level_left[kk - a.k_first] = n_alive;
         if (n_alive == 0) break;
+        if (a.k_last > 0 && k_next > a.k_last) break;
         kmax = k_next - 1;
         k = k_next;
     }
@@ -728,6 +735,36 @@ __global__ void k_mask_from_state(const int32_t* __restrict__ t,
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < m; c += stride)
         mask[c] = t[inv[c]] == 0 ? 1 : 0;
+}
+
+// The same mask in two passes: one bit per internal edge (coalesced over the
+// states; the bitmap, 1/32 of them, stays in L2), then a gather of bits in
+// canonical order, four edges per thread in flight (a gather of the states
+// themselves reads a 32-byte sector per edge).
+__global__ void k_alive_bits(const int32_t* __restrict__ t, int64_t m,
+                             unsigned int* __restrict__ bits) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < m;
+         base += nw * 32) {
+        const int64_t j = base + lane;
+        const unsigned b = __ballot_sync(0xffffffffu, j < m && t[j] == 0);
+        if (lane == 0) bits[base >> 5] = b;
+    }
+}
+
+__global__ void k_mask_from_bits(const unsigned int* __restrict__ bits,
+                                 const int32_t* __restrict__ inv, int64_t m,
+                                 uint8_t* __restrict__ mask) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c0 < m; c0 += 4 * stride) {
+        int32_t j[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) j[u] = c0 + u * stride < m ? inv[c0 + u * stride] : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (j[u] >= 0) mask[c0 + u * stride] = (bits[j[u] >> 5] >> (j[u] & 31)) & 1u;
+    }
 }
 
 __global__ void k_resume_states(int32_t* __restrict__ t, int64_t m) {
@@ -785,6 +822,7 @@ struct PeelPlan {
     bool resume = false;       // start from the graph's cached k-truss
     bool cache = false;        // state/support (and adjacency) are the graph's cache
     bool fresh_adj = true;     // the working adjacency must be copied from the graph
+    bool readonly_adj = false; // ... or the graph's own is read in place (one level)
     uint8_t* out_mask = nullptr;    // single level: canonical k-truss mask
     int32_t* out_truss = nullptr;   // decomposition: canonical truss numbers
     bool build_lists = false;  // the lists are built by this peel (else cached)
@@ -825,6 +863,8 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
     if (!g->support_valid) return fail(TC_EINVAL, "internal: peel planned without supports");
     p.g = g;
     p.single = single;
+    p.readonly_adj = false;
+    p.fresh_adj = true;
     PeelArgs& a = p.a;
     a = PeelArgs{};
     a.m = m;
@@ -865,8 +905,11 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
             p.ix = false;
             entries = full;
         } else if (forced != PEEL_LISTS || full >= 0xffffffffLL) {
-            TC_TRY(partial_list_entries(g, LIST_BOUND, &entries, &p.lists.low_edges,
-                                        g->last_stream));
+            if (g->tri_valid && g->tri_bound == LIST_BOUND)
+                entries = g->tri_entries;  // the graph keeps these lists: nothing to count
+            else
+                TC_TRY(partial_list_entries(g, LIST_BOUND, &entries, &p.lists.low_edges,
+                                            g->last_stream));
             const bool held = g->tri_off && g->tri_bound == LIST_BOUND;
             if (entries < 0xffffffffLL &&
                 (forced == PEEL_HYBRID ||
@@ -938,16 +981,24 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
             a.eid = g->kt_eid;
             a.rowlen = g->kt_rowlen;
         } else {
-            p.fresh_adj = true;
-            TC_TRY(sc.alloc(&a.rowlen, g->n));
-            TC_TRY(sc.alloc(&a.col, 2 * m));
-            TC_TRY(sc.alloc(&a.eid, 2 * m));
+            p.readonly_adj = true;
         }
         g->kt_adj = false;  // valid again only if this peel completes in the graph's buffers
+    } else if (single) {
+        p.readonly_adj = true;
     } else {
         TC_TRY(sc.alloc(&a.rowlen, g->n));
         TC_TRY(sc.alloc(&a.col, 2 * m));
         TC_TRY(sc.alloc(&a.eid, 2 * m));
+    }
+    if (p.readonly_adj) {
+        // one level: the intersections read the graph's own adjacency, with
+        // dead entries left in place (no compaction), instead of a copy
+        p.fresh_adj = false;
+        a.no_compact = 1;
+        a.col = g->col;
+        a.eid = g->eid;
+        TC_TRY(sc.alloc(&a.rowlen, g->n));
     }
     if (p.cache) a.s = g->kt_support;
     else TC_TRY(sc.alloc(&a.s, m));
@@ -955,8 +1006,14 @@ int peel_plan(PeelPlan* pp, Scratch& sc, Graph* g, int32_t k_first, bool single,
     // intersection form has none)
     const int64_t heavy_cap = p.tl ? std::min<int64_t>(m, entries / HEAVY + 1) : 1;
     for (int i = 0; i < 2; ++i) {
-        TC_TRY(sc.alloc(&a.A[i], m));
-        TC_TRY(sc.alloc(&a.W[i], m));
+        // one level: no alive list or window is written; A[0] only holds
+        // the mask's bitmap afterwards (one bit per edge)
+        if (!single) {
+            TC_TRY(sc.alloc(&a.A[i], m));
+            TC_TRY(sc.alloc(&a.W[i], m));
+        } else if (i == 0) {
+            TC_TRY(sc.alloc(&a.A[0], m / 32 + 1));
+        }
         TC_TRY(sc.alloc(&a.F[i], m));
         TC_TRY(sc.alloc(&a.H[i], heavy_cap));
         if (p.tl) {
@@ -996,7 +1053,10 @@ int peel_enqueue(PeelPlan* pp, cudaStream_t s) {
     const int64_t m = g->m;
     if (p.tl && p.build_lists)
         TC_TRY(enqueue_triangle_lists(g, g->support, p.off, p.pairs, &p.lists, s));
-    if (p.ix && p.fresh_adj) {
+    if (p.ix && p.readonly_adj) {
+        k_peel_init<<<small_grid(g->n), 256, 0, s>>>(g->rowptr, g->n, a.rowlen);
+        TC_LAUNCH_CHECK("k_peel_init");
+    } else if (p.ix && p.fresh_adj) {
         TC_CUDA_TRY(cudaMemcpyAsync(a.col, g->col, sizeof(int32_t) * 2 * m,
                                     cudaMemcpyDeviceToDevice, s));
         TC_CUDA_TRY(cudaMemcpyAsync(a.eid, g->eid, sizeof(int32_t) * 2 * m,
@@ -1018,7 +1078,13 @@ int peel_enqueue(PeelPlan* pp, cudaStream_t s) {
     TC_CUDA_TRY(cudaMemsetAsync(a.ctl, 0, sizeof(PeelCtl), s));
     void* params[] = {&a};
     TC_TRY(p.timer.start(s));
-    TC_CUDA_TRY(cudaLaunchCooperativeKernel(p.fn, dim3(p.blocks), dim3(PK_THREADS), params, 0, s));
+    // one block is always resident: its grid barrier needs no cooperative
+    // launch, and a plain launch can run beside other streams' cooperative ones
+    if (p.blocks == 1)
+        TC_CUDA_TRY(cudaLaunchKernel(p.fn, dim3(1), dim3(PK_THREADS), params, 0, s));
+    else
+        TC_CUDA_TRY(cudaLaunchCooperativeKernel(p.fn, dim3(p.blocks), dim3(PK_THREADS), params, 0,
+                                                s));
     count_launch();
     TC_TRY(p.timer.stop(s));
     if (!p.single && p.out_truss) {
@@ -1026,8 +1092,12 @@ int peel_enqueue(PeelPlan* pp, cudaStream_t s) {
         TC_LAUNCH_CHECK("k_truss_from_state");
     }
     if (p.single && p.out_mask) {
-        k_mask_from_state<<<small_grid(m), 256, 0, s>>>(a.t, g->inv, m, p.out_mask);
-        TC_LAUNCH_CHECK("k_mask_from_state");
+        // the peel's alive lists are free now: the first holds the bitmap
+        unsigned int* bits = reinterpret_cast<unsigned int*>(a.A[0]);
+        k_alive_bits<<<small_grid(m), 256, 0, s>>>(a.t, m, bits);
+        TC_LAUNCH_CHECK("k_alive_bits");
+        k_mask_from_bits<<<small_grid(m), 256, 0, s>>>(bits, g->inv, m, p.out_mask);
+        TC_LAUNCH_CHECK("k_mask_from_bits");
     }
     return TC_OK;
 }
@@ -1085,16 +1155,19 @@ namespace {
 // Plan, run and complete one peel on the graph's stream; results go to the
 // canonical-order output (mask for one level, truss numbers otherwise).
 int run_peel(Graph* g, int32_t k_first, bool single, uint8_t* out_mask, int32_t* out_truss,
-             PeelCtl* result, cudaStream_t s) {
+             PeelCtl* result, cudaStream_t s, int32_t k_last = 0,
+             long long* level_left = nullptr) {
     TC_TRY(ensure_support_impl(g, s));
     Scratch sc(s);
     int32_t* t;
     TC_TRY(sc.alloc(&t, g->m));
     PeelPlan p;
     TC_TRY(peel_plan(&p, sc, g, k_first, single, t, PEEL_AUTO, /*keep_lists=*/true,
-                     /*use_cache=*/single));
+                     /*use_cache=*/single && g->keep_results, g->peel_max_blocks));
     p.out_mask = out_mask;
     p.out_truss = out_truss;
+    p.a.k_last = k_last;
+    p.a.level_left = level_left;
     TC_TRY(peel_enqueue(&p, s));
     TC_TRY(peel_finish(&p, s, nullptr, nullptr));
     *result = p.result;
@@ -1131,7 +1204,8 @@ __global__ void k_mask_from_truss(const int32_t* __restrict__ truss, int64_t m, 
 
 // A test hook forcing a peel form always peels.
 bool truss_cache_usable(const Graph* g) {
-    return g->truss_valid && peel_mode() == PEEL_AUTO && intersect_mode() == 0;
+    return g->keep_results && g->truss_valid && peel_mode() == PEEL_AUTO &&
+           intersect_mode() == 0;
 }
 }  // namespace
 
@@ -1158,6 +1232,66 @@ int peel_ktruss(Graph* g, int32_t k, uint8_t* mask, int64_t* edges_left, cudaStr
     return TC_OK;
 }
 
+namespace {
+// Counts, per k in [k_lo, k_hi], the edges with truss number >= k.
+__global__ void k_truss_counts(const int32_t* __restrict__ truss, int64_t m, int32_t k_lo,
+                               int32_t k_hi, unsigned long long* __restrict__ counts) {
+    __shared__ unsigned long long sh[64];
+    const int nk = k_hi - k_lo + 1;
+    for (int i = threadIdx.x; i < nk; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int32_t t = truss[e];
+        if (t >= k_lo) atomicAdd(&sh[min(t, k_hi) - k_lo], 1ull);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nk; i += blockDim.x)
+        if (sh[i]) atomicAdd(&counts[i], sh[i]);
+}
+}  // namespace
+
+int peel_sizes(Graph* g, int32_t k_lo, int32_t k_hi, int64_t* sizes, cudaStream_t s) {
+    const int64_t m = g->m;
+    const int nk = k_hi - k_lo + 1;
+    int32_t k = k_lo;
+    for (; k <= 2 && k <= k_hi; ++k) sizes[k - k_lo] = m;  // the 2-truss is every edge
+    if (k > k_hi) return TC_OK;
+    if (m == 0) {
+        for (; k <= k_hi; ++k) sizes[k - k_lo] = 0;
+        return TC_OK;
+    }
+    Scratch sc(s);
+    if (truss_cache_usable(g)) {
+        // the kept decomposition: count truss numbers >= k (suffix sums of a histogram)
+        unsigned long long* cnt;
+        TC_TRY(sc.alloc(&cnt, nk));
+        TC_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * nk, s));
+        k_truss_counts<<<small_grid(m), 256, 0, s>>>(g->truss_cache, m, k, k_hi, cnt + (k - k_lo));
+        TC_LAUNCH_CHECK("k_truss_counts");
+        unsigned long long h[64] = {};
+        TC_CUDA_TRY(cudaMemcpyAsync(h, cnt, sizeof(unsigned long long) * nk,
+                                    cudaMemcpyDeviceToHost, s));
+        TC_CUDA_TRY(cudaStreamSynchronize(s));
+        unsigned long long run = 0;
+        for (int32_t kk = k_hi; kk >= k; --kk) {
+            run += h[kk - k_lo];
+            sizes[kk - k_lo] = (int64_t)run;
+        }
+        return TC_OK;
+    }
+    long long* left;
+    TC_TRY(sc.alloc(&left, nk));
+    TC_CUDA_TRY(cudaMemsetAsync(left, 0, sizeof(long long) * nk, s));  // emptied levels stay 0
+    PeelCtl r{};
+    TC_TRY(run_peel(g, k, false, nullptr, nullptr, &r, s, k_hi, left + (k - k_lo)));
+    long long h[64] = {};
+    TC_CUDA_TRY(cudaMemcpyAsync(h, left, sizeof(long long) * nk, cudaMemcpyDeviceToHost, s));
+    TC_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int32_t kk = k; kk <= k_hi; ++kk) sizes[kk - k_lo] = h[kk - k_lo];
+    return TC_OK;
+}
+
 int peel_decompose(Graph* g, int32_t* truss, int32_t* kmax, cudaStream_t s) {
     const int64_t m = g->m;
     if (m == 0) {
@@ -1176,7 +1310,8 @@ int peel_decompose(Graph* g, int32_t* truss, int32_t* kmax, cudaStream_t s) {
     // keep the decomposition when it fits the graph's optional memory
     size_t free_b = 0, total_b = 0;
     TC_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    bool room = may_keep(g, 4.0 * (double)m, g->truss_cache != nullptr, 0.4 * (double)free_b);
+    bool room = g->keep_results &&
+                may_keep(g, 4.0 * (double)m, g->truss_cache != nullptr, 0.4 * (double)free_b);
     if (!room && g->truss_cache) {
         dev_free(g->truss_cache, s);
         g->truss_cache = nullptr;

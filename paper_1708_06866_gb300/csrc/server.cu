@@ -7,10 +7,16 @@
 // resident or can be made resident within the device-memory budget after
 // evicting least-recently-used idle graphs.  Graphs are built on first use
 // from the caller's host edge lists.  Work of requests that arrive while
-// others run overlaps on the device.  A graph's first k-truss request
-// computes its truss decomposition, which the library keeps with the graph,
-// so later k-truss requests on it are threshold passes (Section III-B: the
-// k-trusses nest).
+// others run overlaps on the device.  By default a graph's first k-truss
+// request computes its truss decomposition, which the library keeps with the
+// graph, so later k-truss requests on it are threshold passes (Section
+// III-B: the k-trusses nest); with results not kept
+// (tc_server_set_result_cache) every k-truss request peels on the device.
+// With more than one slot, a slot that takes a request also takes the
+// other requests for the same graph that have arrived and wait (coalescing,
+// up to MAX_GROUP): their counts come from one count call and their k-truss
+// sizes from one ktruss_sizes peel over their range of k.  One slot is the
+// plain loop: one request per call, in arrival order.
 //
 // Test hook: a fake mode runs the same scheduler with sleeps instead of
 // device work (no CUDA calls), so its host logic is testable without a GPU.
@@ -27,6 +33,7 @@
 namespace {
 
 std::atomic<int> g_server_fake{0};
+constexpr int MAX_GROUP = 64;  // requests answered by one slot's turn
 
 using Clock = std::chrono::steady_clock;
 
@@ -58,6 +65,7 @@ struct tc_server {
     bool fake = false;
     int64_t budget = 0;
     int64_t opt_per_pair = 0;
+    bool keep_results = true;
     int64_t reserved = 0;
     uint64_t tick = 0;
     tc_server_stats stats{};
@@ -95,7 +103,7 @@ int execute(tc_server* s, Slot& slot, int32_t gid, const tc_request& rq, int64_t
     }
     if (rq.kind == TC_REQ_COUNT) return tc_count(e.g, result, slot.stream);
     if (rq.kind != TC_REQ_KTRUSS) return tc::fail(TC_EINVAL, "server: unknown request kind");
-    if (!e.indexed && !e.index_tried) {
+    if (s->keep_results && !e.indexed && !e.index_tried) {
         e.index_tried = true;
         int32_t kmax = 0;
         TC_TRY(ktruss_max(e.g, &kmax, nullptr, slot.stream));
@@ -114,6 +122,52 @@ int execute(tc_server* s, Slot& slot, int32_t gid, const tc_request& rq, int64_t
     return ktruss(e.g, rq.k, slot.mask, result, slot.stream);
 }
 
+// Answers requests reqs[ids[0..cnt)] (all on graph gid): counts from one
+// call, k-truss sizes from one ktruss_sizes over their k range (or one
+// ktruss when a single k-truss request is in the group).
+int execute_group(tc_server* s, Slot& slot, int32_t gid, const tc_request* reqs,
+                  const int64_t* ids, int cnt, int64_t* results) {
+    if (cnt == 1 || s->fake) {
+        for (int i = 0; i < cnt; ++i) TC_TRY(execute(s, slot, gid, reqs[ids[i]], &results[i]));
+        return TC_OK;
+    }
+    Entry& e = s->graphs[gid];
+    int32_t klo = INT32_MAX, khi = 0, nk = 0;
+    bool any_count = false;
+    for (int i = 0; i < cnt; ++i) {
+        const tc_request& rq = reqs[ids[i]];
+        if (rq.kind == TC_REQ_COUNT) {
+            any_count = true;
+        } else {
+            klo = std::min(klo, rq.k);
+            khi = std::max(khi, rq.k);
+            ++nk;
+        }
+    }
+    int64_t T = 0;
+    if (any_count) TC_TRY(tc_count(e.g, &T, slot.stream));
+    int64_t sizes[64];
+    const bool range = nk > 1 && khi - klo < 64;
+    if (range) {
+        if (s->keep_results && !e.indexed && !e.index_tried) {
+            e.index_tried = true;
+            int32_t kmax = 0;
+            TC_TRY(ktruss_max(e.g, &kmax, nullptr, slot.stream));
+            tc_graph_info_t info;
+            TC_TRY(tc_graph_info(e.g, &info, slot.stream));
+            e.indexed = info.truss_cached != 0;
+        }
+        TC_TRY(ktruss_sizes(e.g, klo, khi, sizes, slot.stream));
+    }
+    for (int i = 0; i < cnt; ++i) {
+        const tc_request& rq = reqs[ids[i]];
+        if (rq.kind == TC_REQ_COUNT) results[i] = T;
+        else if (range) results[i] = sizes[rq.k - klo];
+        else TC_TRY(execute(s, slot, gid, rq, &results[i]));
+    }
+    return TC_OK;
+}
+
 int build(tc_server* s, Slot& slot, int32_t gid) {
     Entry& e = s->graphs[gid];
     if (s->fake) {
@@ -123,6 +177,13 @@ int build(tc_server* s, Slot& slot, int32_t gid) {
     }
     const tc_graph_source& g = s->src[gid];
     TC_TRY(tc_build_csr(g.src, g.dst, g.m_in, g.n, TC_INPUT_HOST, slot.stream, &e.g));
+    TC_TRY(tc_graph_set_result_cache(e.g, s->keep_results ? 1 : 0));
+#ifdef TC_SERVE_PEEL_DIV
+    e.g->g.peel_max_blocks = std::max(1, tc::num_sms() / TC_SERVE_PEEL_DIV);
+#endif
+#ifdef TC_SERVE_SMALL_M
+    if (g.m_in <= (int64_t)TC_SERVE_SMALL_M) e.g->g.peel_max_blocks = 1;
+#endif
     return tc_graph_set_memory_limit(e.g, s->opt_per_pair * g.m_in);
 }
 
@@ -131,12 +192,15 @@ void release(tc_server* s, tc_graph* g) {
 }
 
 void worker(tc_server* s, int slot_id, const tc_request* reqs, int64_t nreq, bool open_loop,
-            Clock::time_point t0, std::vector<char>* taken, int64_t* head, int64_t* left,
-            int64_t* running, tc_response* out) {
+            bool coalesce, Clock::time_point t0, std::vector<char>* taken, int64_t* head,
+            int64_t* left, int64_t* running, tc_response* out) {
     if (!s->fake) cudaSetDevice(s->device);
     Slot& slot = s->slots[slot_id];
+    int64_t group[MAX_GROUP];
+    int64_t results[MAX_GROUP];
     for (;;) {
         int64_t pick = -1;
+        int ng = 0;
         std::vector<tc_graph*> evict;
         bool need_build = false;
         {
@@ -182,6 +246,18 @@ void worker(tc_server* s, int slot_id, const tc_request* reqs, int64_t nreq, boo
             (*taken)[pick] = 1;
             const int32_t gid = reqs[pick].graph;
             Entry& e = s->graphs[gid];
+            group[ng++] = pick;
+            if (coalesce) {
+                // the other requests for this graph that have arrived and wait
+                const double now = seconds_since(t0);
+                for (int64_t i = pick + 1; i < nreq && ng < MAX_GROUP; ++i) {
+                    if (open_loop && reqs[i].arrival_s > now) break;
+                    if (!(*taken)[i] && reqs[i].graph == gid) {
+                        (*taken)[i] = 1;
+                        group[ng++] = i;
+                    }
+                }
+            }
             e.busy = true;
             e.last_use = ++s->tick;
             if (!e.resident) {
@@ -218,9 +294,7 @@ void worker(tc_server* s, int slot_id, const tc_request* reqs, int64_t nreq, boo
         for (tc_graph* g : evict) release(s, g);
         const tc_request& rq = reqs[pick];
         Entry& e = s->graphs[rq.graph];
-        tc_response& r = out[pick];
-        r.slot = slot_id;
-        r.start_s = seconds_since(t0);
+        const double start_s = seconds_since(t0);
         int rc = TC_OK;
         if (need_build) {
             rc = build(s, slot, rq.graph);
@@ -235,16 +309,21 @@ void worker(tc_server* s, int slot_id, const tc_request* reqs, int64_t nreq, boo
                 e.g = nullptr;
             }
         }
-        int64_t result = 0;
-        if (rc == TC_OK) rc = execute(s, slot, rq.graph, rq, &result);
+        if (rc == TC_OK) rc = execute_group(s, slot, rq.graph, reqs, group, ng, results);
         int64_t held = -1;
         if (rc == TC_OK && !s->fake) {
             tc_graph_info_t info;
             if (tc_graph_info(e.g, &info, slot.stream) == TC_OK) held = info.device_bytes;
         }
-        r.done_s = seconds_since(t0);
-        r.result = result;
-        r.status = rc;
+        const double done_s = seconds_since(t0);
+        for (int i = 0; i < ng; ++i) {
+            tc_response& r = out[group[i]];
+            r.slot = slot_id;
+            r.start_s = start_s;
+            r.done_s = done_s;
+            r.result = rc == TC_OK ? results[i] : 0;
+            r.status = rc;
+        }
         {
             std::lock_guard<std::mutex> lk(s->mu);
             // what the graph holds now (kept supports, lists, truss numbers)
@@ -256,8 +335,8 @@ void worker(tc_server* s, int slot_id, const tc_request* reqs, int64_t nreq, boo
             }
             e.busy = false;
             --*running;
-            --*left;
-            if (rc != TC_OK) ++s->stats.errors;
+            *left -= ng;
+            if (rc != TC_OK) s->stats.errors += ng;
         }
         s->cv.notify_all();
     }
@@ -324,8 +403,8 @@ int tc_server_run(tc_server* s, const tc_request* reqs, int64_t num_reqs, int32_
     std::vector<std::thread> th;
     th.reserve(use);
     for (int i = 0; i < use; ++i)
-        th.emplace_back(worker, s, i, reqs, num_reqs, open_loop != 0, t0, &taken, &head, &left,
-                        &running, out);
+        th.emplace_back(worker, s, i, reqs, num_reqs, open_loop != 0, use > 1, t0, &taken, &head,
+                        &left, &running, out);
     for (auto& t : th) t.join();
     if (wall_s) *wall_s = seconds_since(t0);
     if (!s->fake)
@@ -357,6 +436,23 @@ void tc_server_destroy(tc_server* s) {
         }
     }
     delete s;
+}
+
+int tc_server_set_result_cache(tc_server* s, int32_t keep) {
+    if (!s) return tc::fail(TC_EINVAL, "server: NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->keep_results = keep != 0;
+    for (Entry& e : s->graphs) {
+        if (!s->fake && e.resident && e.g) {
+            const int rc = tc_graph_set_result_cache(e.g, keep);
+            if (rc != TC_OK) return rc;
+        }
+        if (!s->keep_results) {
+            e.indexed = false;
+            e.index_tried = false;
+        }
+    }
+    return TC_OK;
 }
 
 int tc_debug_server_fake(int on) { return g_server_fake.exchange(on ? 1 : 0); }

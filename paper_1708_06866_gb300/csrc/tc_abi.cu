@@ -107,6 +107,8 @@ void free_graph(Graph* g) {
     dev_free(g->col, s);
     dev_free(g->eid, s);
     dev_free(g->inv, s);
+    dev_free(g->head, s);
+    dev_free(g->iend, s);
     dev_free(g->oshift, s);
     dev_free(g->support, s);
     dev_free(g->tri_off, s);
@@ -326,6 +328,18 @@ int ktruss_max(tc_graph* g, int32_t* kmax_out, int32_t* truss_out, void* cuda_st
     return TC_OK;
 }
 
+int ktruss_sizes(tc_graph* g, int32_t k_lo, int32_t k_hi, int64_t* sizes_out, void* cuda_stream) {
+    TC_TRY(begin_call(g, cuda_stream));
+    if (!sizes_out) return fail(TC_EINVAL, "sizes_out is NULL");
+    if (k_lo < 2 || k_hi < k_lo || k_hi - k_lo >= 64)
+        return fail(TC_EINVAL, "ktruss_sizes: need 2 <= k_lo <= k_hi < k_lo + 64");
+    tc::Graph* gg = &g->g;
+    DeviceGuard dg(gg->device);
+    cudaStream_t s = as_stream(cuda_stream);
+    TC_TRY(tc::peel_sizes(gg, k_lo, k_hi, sizes_out, s));
+    return tc::check_dev_err(gg->dev_err, s);
+}
+
 int64_t tc_num_edges(const tc_graph* g) { return g ? g->g.m : -1; }
 
 int32_t tc_num_vertices(const tc_graph* g) { return g ? g->g.n : -1; }
@@ -352,7 +366,7 @@ int tc_graph_info(const tc_graph* g, tc_graph_info_t* info, void* cuda_stream) {
     info->wedge_work = ww;
     const int64_t m = gg->m, n = gg->n;
     // lo, hi, ends, inv (m each) and col, eid (2m each); rowptr, upper, oshift
-    info->device_bytes = m * (4 + 4 + 8 + 4 + 8 + 8) + 8 * (n + 1) + 8 * n + 8 * n +
+    info->device_bytes = m * (4 + 4 + 8 + 4 + 8 + 8 + 8) + 8 * (n + 1) + 8 * n + 8 * n +
                          (gg->support ? 4 * m : 0) +
                          (gg->tri_valid ? 8 * (m + 1) + 8 * gg->tri_entries : 0) +
                          (gg->kt_state ? 8 * m : 0) + (gg->truss_cache ? 4 * m : 0) + (gg->kt_col ? 16 * m + 4 * n : 0);
@@ -385,6 +399,29 @@ int tc_graph_wedge_work(tc_graph* g, int64_t* out, void* cuda_stream) {
 int tc_graph_set_memory_limit(tc_graph* g, int64_t bytes) {
     if (!g) return fail(TC_EINVAL, "graph is NULL");
     g->g.mem_limit = bytes < 0 ? -1 : bytes;
+    return TC_OK;
+}
+
+int tc_graph_set_result_cache(tc_graph* g, int32_t keep) {
+    if (!g) return fail(TC_EINVAL, "graph is NULL");
+    DeviceGuard dg(g->g.device);
+    tc::Graph* gg = &g->g;
+    gg->keep_results = keep != 0;
+    if (!gg->keep_results) {
+        cudaStream_t s = gg->last_stream;
+        tc::dev_free(gg->truss_cache, s);
+        tc::dev_free(gg->kt_state, s);
+        tc::dev_free(gg->kt_support, s);
+        tc::dev_free(gg->kt_col, s);
+        tc::dev_free(gg->kt_eid, s);
+        tc::dev_free(gg->kt_rowlen, s);
+        gg->truss_cache = nullptr;
+        gg->kt_state = gg->kt_support = nullptr;
+        gg->kt_col = gg->kt_eid = gg->kt_rowlen = nullptr;
+        gg->truss_valid = false;
+        gg->kt_k = 0;
+        gg->kt_adj = false;
+    }
     return TC_OK;
 }
 

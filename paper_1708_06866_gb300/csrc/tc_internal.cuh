@@ -244,12 +244,21 @@ struct Graph {
     int32_t* col = nullptr;   // 2m neighbour rank ids
     int32_t* eid = nullptr;   // 2m internal edge ids
     int32_t* inv = nullptr;   // internal id of each canonical edge
+    // for the column kernel: head[e] = the higher-rank end of internal edge
+    // e (the out-lists laid out by edge id); iend[i] = one past the last
+    // out-edge id of the i-th in-neighbour entry's neighbour, in-entries
+    // numbered row by row (row v's start at rowptr[v] - first edge id of v)
+    int32_t* head = nullptr;  // m
+    int32_t* iend = nullptr;  // m
     // internal ids follow the out-lists: the out-entry at position p of row r
     // is edge p - oshift[r] (n entries)
     int64_t* oshift = nullptr;
     int32_t max_out = 0;      // max |N+(u)|
     int32_t max_deg = 0;
-    int32_t light_rows = 0;   // rows of degree <= LIGHT_DEG (the lowest ranks)
+    // rows of degree <= 16, 32, 64, 128 (LIGHT_DEG): the lowest ranks
+    int32_t light_rows[4] = {0, 0, 0, 0};
+    // the column kernel's light columns: degree <= this bound (16..LIGHT_DEG)
+    int32_t col_light_deg = LIGHT_DEG;
     int64_t wedge_work = -1;  // sum of |N+(u)| + |N+(v)| over oriented edges (lazy)
     int64_t column_work = -1; // sum over u of |N+(u)| (|N+(u)| - 1) / 2 (lazy, with wedge_work)
     int64_t last_peel_rounds = 0;  // bulk rounds of the most recent peel
@@ -291,6 +300,11 @@ struct Graph {
     // bound on optional device memory for this graph (triangle lists, their
     // cache, the cached compacted adjacency); -1 = a share of free memory
     int64_t mem_limit = -1;
+    // keep results between calls (truss numbers, the latest k-truss state)
+    bool keep_results = true;
+    // cap on the peel's grid (0: none): a server shares the device between
+    // concurrent requests
+    int peel_max_blocks = 0;
     int64_t triangles = -1;
     int* dev_err = nullptr;
     unsigned long long* dev_scalars = nullptr;  // small device scratch (8 words)
@@ -362,6 +376,9 @@ bool triangle_lists_supported(const Graph* g);
 int build_triangle_lists(Graph* g, const int32_t* sup, unsigned long long* off, int2* pairs,
                          cudaStream_t s);
 int peel_decompose(Graph* g, int32_t* truss_dev, int32_t* kmax, cudaStream_t s);
+// Sizes of the k-trusses for k = k_lo .. k_hi (at most 64 values; host
+// output): the decomposition's levels from one peel, stopping after k_hi.
+int peel_sizes(Graph* g, int32_t k_lo, int32_t k_hi, int64_t* sizes, cudaStream_t s);
 // Connected components of the k-truss: canonical-order edge labels (device,
 // m), optional vertex labels (device, n); labels are smallest vertex ids.
 int truss_components(Graph* g, int32_t k, int32_t* edge_label, int32_t* vertex_label,

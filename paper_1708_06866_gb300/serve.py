@@ -47,7 +47,7 @@ class NativeServer:
     host int32 edge lists (kept referenced while the server lives)."""
 
     def __init__(self, pool: Dict[int, tuple], slots: int = 8, budget_bytes: int = 120 << 30,
-                 optional_bytes_per_pair: int = 40):
+                 optional_bytes_per_pair: int = 40, keep_results: bool = True):
         self.lib = tc.load_library()
         self.handle = None
         self.ids = sorted(pool)
@@ -71,6 +71,14 @@ class NativeServer:
                                             ctypes.byref(h)), "tc_server_create")
         self.handle = h.value
         self.slots = slots
+        if not keep_results:
+            self.set_result_cache(False)
+
+    def set_result_cache(self, keep: bool):
+        """keep=False: every k-truss request peels on the device (no kept
+        truss decompositions or k-truss states)."""
+        tc._check(self.lib.tc_server_set_result_cache(self.handle, 1 if keep else 0),
+                  "tc_server_set_result_cache")
 
     def run(self, trace, open_loop: bool = True, slots: int = 0) -> float:
         """Serves [(arrival seconds, Request)] in order; fills each Request's

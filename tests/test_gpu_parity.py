@@ -616,3 +616,40 @@ def test_memory_bound_counts_everything_kept_together():
     assert info2["peel_lists"] == 0 and info2["truss_cached"] == 1
     assert info2["device_bytes"] < info["device_bytes"]
     tc.tc_graph_free(g)
+
+
+@pytest.mark.parametrize("case", ["rmat", "er", "king", "complete"])
+def test_ktruss_sizes_against_oracle(case):
+    """The sizes of the k-trusses for a range of k (one peel over levels
+    k_lo..k_hi) equal the oracle's decomposition levels, in every peel form,
+    with results not kept (a peel per call) and from kept truss numbers."""
+    if case == "rmat":
+        s, d, n = graphgen.rmat(12, seed=41)
+    elif case == "er":
+        s, d, n = graphgen.er(2000, 16000, seed=42)
+    elif case == "king":
+        s, d, n = graphgen.king(40)
+    else:
+        s, d, n = graphgen.complete(30)
+    og = oracle.OracleGraph.from_edges(s, d, n)
+    want = [og.m] + og.truss_levels(12)          # k = 2 .. 12
+    g = tc.tc_build_csr(dev(s), dev(d), n)
+    tc.tc_graph_set_result_cache(g, False)
+    for mode in PEEL_MODES.values():
+        prev = tc.tc_debug_peel_mode(mode)
+        try:
+            assert tc.ktruss_sizes(g, 2, 12) == want, mode
+            assert tc.ktruss_sizes(g, 5, 7) == want[3:6], mode
+            assert tc.ktruss_sizes(g, 9, 9) == [want[7]], mode
+        finally:
+            tc.tc_debug_peel_mode(prev)
+    tc.tc_graph_set_result_cache(g, True)
+    tc.ktruss_max(g)                              # kept truss numbers answer now
+    assert tc.tc_graph_info(g)["truss_cached"] == 1
+    assert tc.ktruss_sizes(g, 2, 12) == want
+    assert tc.ktruss_sizes(g, 4, 10) == want[2:9]
+    for bad in ((1, 5), (3, 2), (3, 67)):
+        with pytest.raises(tc.TCError) as ei:
+            tc.ktruss_sizes(g, *bad)
+        assert ei.value.code == tc.TC_EINVAL
+    tc.tc_graph_free(g)

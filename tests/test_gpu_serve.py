@@ -71,9 +71,11 @@ def test_budget_forces_eviction_and_rebuild_on_gpu():
 
 def test_failed_allocation_fails_one_request_and_the_server_goes_on():
     """An injected device-allocation failure during a run (on the host: the
-    library's allocation hook) fails the request that hit it with TC_ENOMEM;
-    every other request in the run still gets its exact result, and the next
-    run on the same server succeeds throughout."""
+    library's allocation hook) fails the call that hit it with TC_ENOMEM —
+    the requests that call answered (several, when same-graph requests were
+    coalesced) report the error; every other request in the run still gets
+    its exact result, and the next run on the same server succeeds
+    throughout."""
     pool = graphgen.rmat_pool(6, seed=21, n_min=1 << 8, n_max=1 << 11)
     alone = alone_results(pool)
     srv = serve.NativeServer(pool, slots=3, budget_bytes=4 << 30)
@@ -84,8 +86,9 @@ def test_failed_allocation_fails_one_request_and_the_server_goes_on():
     finally:
         tc.tc_debug_fail_alloc(0)
     failed = [r for _, r in trace if r.error is not None]
-    assert 1 <= len(failed) <= 2, [r.error for r in failed]
+    assert len(failed) >= 1, [r.error for r in failed]
     assert all("code -3" in r.error for r in failed)
+    assert len({(r.slot, r.start) for r in failed}) <= 2   # at most two calls failed
     for _, r in trace:
         if r.error is None:
             assert r.result == alone[(r.graph, r.kind, r.k)], r

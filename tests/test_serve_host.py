@@ -85,3 +85,28 @@ def test_bad_requests_and_arguments_are_refused(fake):
         serve.NativeServer(pool_of([10]), slots=0)
     with pytest.raises(tc.TCError):
         serve.NativeServer(pool_of([10]), budget_bytes=0)
+
+
+def test_waiting_requests_for_one_graph_are_answered_together(fake):
+    """With several slots, a slot that takes a request also takes the
+    requests for the same graph that have arrived and wait: they share one
+    call (same slot, same start), each with its own result.  One slot is the
+    plain loop: every request its own call."""
+    srv = serve.NativeServer(pool_of([100] * 3), slots=2, budget_bytes=1 << 40)
+    trace = [(0.0, serve.Request(i, i % 3, "ktruss" if i % 2 else "count", 3 + i % 5))
+             for i in range(30)]
+    for _, r in trace:
+        if r.kind == "count":
+            r.k = 0
+    srv.run(trace, open_loop=False)
+    calls = {(r.slot, r.start) for _, r in trace}
+    assert len(calls) < len(trace)            # some calls answered several requests
+    for _, r in trace:
+        assert r.error is None and r.result == expected(r)
+    for (slot, start) in calls:               # a call serves one graph
+        assert len({r.graph for _, r in trace if (r.slot, r.start) == (slot, start)}) == 1
+    one = serve.fresh(trace)
+    srv.run(one, open_loop=False, slots=1)
+    assert len({(r.slot, r.start) for _, r in one}) == len(one)
+    assert all(r.error is None and r.result == expected(r) for _, r in one)
+    srv.close()
