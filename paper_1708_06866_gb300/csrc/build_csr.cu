@@ -58,17 +58,6 @@ struct DedupeOp {
     }
 };
 
-struct UpperOp {  // entries of the symmetric CSR that lie above their row
-    const uint64_t* keys;
-    const uint32_t* eid;
-    int bits;
-    int32_t* fwd;
-    __device__ bool flag(int64_t i) const {
-        const uint64_t k = keys[i];
-        return (k & ((1ull << bits) - 1)) > (k >> bits);
-    }
-    __device__ void emit(int64_t i, int64_t pos) const { fwd[pos] = (int32_t)eid[i]; }
-};
 
 template <typename Op>
 __global__ void __launch_bounds__(CB_THREADS) k_compact_count(Op op, int64_t n,
@@ -108,37 +97,22 @@ __global__ void __launch_bounds__(CB_THREADS) k_compact_write(Op op, int64_t n,
     }
 }
 
-// The chunk totals are uint32 and scanned as uint32: chunk offsets must stay
-// below 2^32, which holds because compaction inputs are below 2^32 entries.
-template <typename Op>
-int compact(const Op& op, int64_t n, int64_t* count_out, uint64_t* scalar_dev, cudaStream_t s) {
-    if (n == 0) {
-        *count_out = 0;
-        return TC_OK;
-    }
-    if (n >= (1ll << 32)) return fail(TC_EOVERFLOW, "compaction input of 2^32 or more entries");
-    const int64_t chunks = (n + CB_CHUNK - 1) / CB_CHUNK;
-    Scratch sc(s);
-    uint32_t* totals;
-    TC_TRY(sc.alloc(&totals, chunks));
-    k_compact_count<Op><<<(unsigned)chunks, CB_THREADS, 0, s>>>(op, n, totals);
-    TC_LAUNCH_CHECK("k_compact_count");
-    TC_TRY(scan_block_totals(totals, chunks, scalar_dev, s));
-    k_compact_write<Op><<<(unsigned)chunks, CB_THREADS, 0, s>>>(op, n, totals);
-    TC_LAUNCH_CHECK("k_compact_write");
-    uint64_t cnt = 0;
-    TC_CUDA_TRY(cudaMemcpyAsync(&cnt, scalar_dev, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-    TC_CUDA_TRY(cudaStreamSynchronize(s));
-    *count_out = (int64_t)cnt;
-    return TC_OK;
-}
-
+// Degrees of the canonical list.  The list is sorted by its lower endpoint,
+// so a warp's 32 consecutive edges mostly share it: lanes with the same
+// lower endpoint add their count with one atomic (the higher endpoints are
+// scattered and take one each).
 __global__ void k_degree(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                          int64_t m, int32_t* __restrict__ deg) {
+    const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-        atomicAdd(&deg[lo[e]], 1);
-        atomicAdd(&deg[hi[e]], 1);
+    // whole warps iterate together (the match needs every lane)
+    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; b < m; b += stride) {
+        const int64_t e = b + lane;
+        const bool ok = e < m;
+        const int32_t a = ok ? lo[e] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, a);
+        if (ok && lane == __ffs(peers) - 1) atomicAdd(&deg[a], __popc(peers));
+        if (ok) atomicAdd(&deg[hi[e]], 1);
     }
 }
 
@@ -158,13 +132,12 @@ __global__ void k_rank(const uint64_t* __restrict__ sorted, int32_t n, int bits,
 }
 
 __global__ void k_pairs(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi, int64_t m,
-                        const int32_t* __restrict__ rank, int bits, int2* __restrict__ ends,
+                        const int32_t* __restrict__ rank, int bits,
                         uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         const int32_t a = rank[lo[e]], c = rank[hi[e]];
         const int32_t u = min(a, c), v = max(a, c);
-        ends[e] = make_int2(u, v);
         keys[2 * e] = ((uint64_t)u << bits) | (uint64_t)v;
         keys[2 * e + 1] = ((uint64_t)v << bits) | (uint64_t)u;
         vals[2 * e] = (uint32_t)e;
@@ -216,30 +189,6 @@ __global__ void k_upper(const uint64_t* __restrict__ keys, int64_t nnz, int bits
     }
 }
 
-// The column kernel's layout of the out-lists by edge id, from the sorted
-// (row, neighbour) keys of the symmetric CSR: an out-entry (neighbour above
-// the row) at position p is edge p - oshift[row], whose head is the
-// neighbour; an in-entry (neighbour u below the row v) is the
-// (p - first edge id of v)-th in-entry overall, and gets u's out-edge end,
-// rowptr[u + 1] - oshift[u].
-__global__ void k_col_aux(const uint64_t* __restrict__ keys, int64_t nnz, int bits,
-                          const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
-                          const int64_t* __restrict__ oshift, int32_t* __restrict__ head,
-                          int32_t* __restrict__ iend) {
-    const uint64_t mask = (1ull << bits) - 1;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
-        const uint64_t k = keys[p];
-        const int32_t r = (int32_t)(k >> bits), c = (int32_t)(k & mask);
-        if (c > r) {
-            head[p - oshift[r]] = c;
-        } else {
-            const int64_t first = upper[r] - oshift[r];  // edge id of r's first out-entry
-            iend[p - first] = (int32_t)(rowptr[c + 1] - oshift[c]);
-        }
-    }
-}
-
 // [0] = largest degree, [1] = largest out-list, [2 + i] = rows of degree
 // at most 16 << i, i < 4 (rows ascend by degree, so these are the rows below
 // that count: the column kernel's light columns for that bound).
@@ -269,9 +218,6 @@ __global__ void k_row_stats(const int64_t* __restrict__ rowptr, const int64_t* _
     }
 }
 
-// Internal edge ids: position in the oriented (u, v) order.  fwd[j] is the
-// canonical id of internal edge j (build time only); inv, kept with the
-// graph, is its inverse.
 __global__ void k_out_degree(const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
                              int32_t n, int32_t* __restrict__ dout) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -290,23 +236,49 @@ __global__ void k_oshift(const int64_t* __restrict__ upper,
         oshift[r] = upper[r] - (int64_t)obase[r];
 }
 
-__global__ void k_invert(const int32_t* __restrict__ fwd, int64_t m, int32_t* __restrict__ inv) {
+// Internal edge ids, from the sorted (row, neighbour) keys of the symmetric
+// CSR and the canonical id each entry carries: an out-entry (neighbour above
+// the row) at position p is internal edge j = p - oshift[row] (a row's
+// out-edges are numbered consecutively), so it records inv[canonical] = j,
+// the edge's ends (row, neighbour) and head (neighbour), and its own edge id;
+// an in-entry (neighbour u below the row v), the
+// (p - first out-edge id of v)-th in-entry overall, records u's out-edge
+// end rowptr[u + 1] - oshift[u] (the column kernel's segment end).  A second
+// pass then gives in-entries their edge ids through inv.  (Internal ids
+// follow the oriented adjacency so that per-edge arrays are read with
+// locality; canonical ids are restored at the ABI boundary.)
+__global__ void k_out_entries(const uint64_t* __restrict__ keys, int32_t* __restrict__ eid,
+                              int64_t nnz, int bits, const int64_t* __restrict__ rowptr,
+                              const int64_t* __restrict__ upper,
+                              const int64_t* __restrict__ oshift, int32_t* __restrict__ inv,
+                              int2* __restrict__ ends, int32_t* __restrict__ head,
+                              int32_t* __restrict__ iend) {
+    const uint64_t mask = (1ull << bits) - 1;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
-        inv[fwd[j]] = (int32_t)j;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
+        const uint64_t k = keys[p];
+        const int32_t r = (int32_t)(k >> bits), c = (int32_t)(k & mask);
+        if (c > r) {
+            const int32_t j = (int32_t)(p - oshift[r]);
+            inv[eid[p]] = j;
+            ends[j] = make_int2(r, c);
+            head[j] = c;
+            eid[p] = j;
+        } else {
+            const int64_t first = upper[r] - oshift[r];  // edge id of r's first out-entry
+            iend[p - first] = (int32_t)(rowptr[c + 1] - oshift[c]);
+        }
+    }
 }
 
-__global__ void k_relabel(int32_t* __restrict__ eid, int64_t nnz, const int32_t* __restrict__ inv) {
+__global__ void k_in_entries(const uint64_t* __restrict__ keys, int32_t* __restrict__ eid,
+                             int64_t nnz, int bits, const int32_t* __restrict__ inv) {
+    const uint64_t mask = (1ull << bits) - 1;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += stride)
-        eid[i] = inv[eid[i]];
-}
-
-__global__ void k_gather_ends(const int2* __restrict__ ends, const int32_t* __restrict__ fwd,
-                              int64_t m, int2* __restrict__ out) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
-        out[j] = ends[fwd[j]];
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
+        const uint64_t k = keys[p];
+        if ((int32_t)(k & mask) < (int32_t)(k >> bits)) eid[p] = inv[eid[p]];
+    }
 }
 
 inline unsigned grid_for(int64_t n, int threads = 256) {
@@ -404,7 +376,7 @@ int build_graph(Graph* g, const int32_t* src, const int32_t* dst, cudaStream_t s
         TC_TRY(sc.alloc(&pvals_alt, nnz));
         pvals = reinterpret_cast<uint32_t*>(g->eid);
         if (m > 0) {
-            k_pairs<<<grid_for(m), 256, 0, s>>>(g->lo, g->hi, m, rank, bits, g->ends, pkeys, pvals);
+            k_pairs<<<grid_for(m), 256, 0, s>>>(g->lo, g->hi, m, rank, bits, pkeys, pvals);
             TC_LAUNCH_CHECK("k_pairs");
             TC_TRY(radix_sort_u64(pkeys, pkeys_alt, pvals, pvals_alt, nnz, 2 * bits, g->dev_err, s));
         }
@@ -415,29 +387,12 @@ int build_graph(Graph* g, const int32_t* src, const int32_t* dst, cudaStream_t s
         if (m > 0) {
             k_upper<<<grid_for(nnz), 256, 0, s>>>(pkeys, nnz, bits, g->upper);
             TC_LAUNCH_CHECK("k_upper");
-            int64_t cnt = 0;
-            int32_t* fwd;  // canonical id of each internal edge
-            TC_TRY(sc.alloc(&fwd, m));
-            UpperOp up{pkeys, pvals, bits, fwd};
-            TC_TRY(compact(up, nnz, &cnt, scalar, s));
-            if (cnt != m) return fail(TC_ECUDA, "internal: oriented edge count mismatch");
-            // renumber edges in oriented order: a row's edges become contiguous,
-            // so per-edge arrays indexed by these ids are read and updated with
-            // locality (canonical ids are restored at the ABI boundary)
-            int2* ends2;
-            TC_TRY(dev_alloc_n(&ends2, m, s));
-            k_invert<<<grid_for(m), 256, 0, s>>>(fwd, m, g->inv);
-            TC_LAUNCH_CHECK("k_invert");
-            k_relabel<<<grid_for(nnz), 256, 0, s>>>(g->eid, nnz, g->inv);
-            TC_LAUNCH_CHECK("k_relabel");
-            k_gather_ends<<<grid_for(m), 256, 0, s>>>(g->ends, fwd, m, ends2);
-            TC_LAUNCH_CHECK("k_gather_ends");
-            dev_free(g->ends, s);
-            g->ends = ends2;
         }
+        // out-edge numbering: the first out-edge of row r is edge obase[r]
+        // (the out-degrees before r); obase[n] must be m
+        unsigned long long* obase;
         {
             int32_t* dout;
-            unsigned long long* obase;
             TC_TRY(sc.alloc(&dout, n));
             TC_TRY(sc.alloc(&obase, (int64_t)n + 1));
             k_out_degree<<<grid_for(n), 256, 0, s>>>(g->rowptr, g->upper, n, dout);
@@ -450,16 +405,23 @@ int build_graph(Graph* g, const int32_t* src, const int32_t* dst, cudaStream_t s
         TC_TRY(dev_alloc_n(&g->head, m, s));
         TC_TRY(dev_alloc_n(&g->iend, m, s));
         if (m > 0) {
-            k_col_aux<<<grid_for(nnz), 256, 0, s>>>(pkeys, nnz, bits, g->rowptr, g->upper,
-                                                    g->oshift, g->head, g->iend);
-            TC_LAUNCH_CHECK("k_col_aux");
+            int32_t* eid = g->eid;  // canonical ids from the sort, internal ids after
+            k_out_entries<<<grid_for(nnz), 256, 0, s>>>(pkeys, eid, nnz, bits, g->rowptr, g->upper,
+                                                        g->oshift, g->inv, g->ends, g->head,
+                                                        g->iend);
+            TC_LAUNCH_CHECK("k_out_entries");
+            k_in_entries<<<grid_for(nnz), 256, 0, s>>>(pkeys, eid, nnz, bits, g->inv);
+            TC_LAUNCH_CHECK("k_in_entries");
         }
         TC_CUDA_TRY(cudaMemsetAsync(g->dev_scalars, 0, 6 * sizeof(unsigned long long), s));
         k_row_stats<<<grid_for(n), 256, 0, s>>>(g->rowptr, g->upper, n, g->dev_scalars);
         TC_LAUNCH_CHECK("k_row_stats");
-        unsigned long long st[6];
+        TC_CUDA_TRY(cudaMemcpyAsync(g->dev_scalars + 6, obase + n, sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToDevice, s));
+        unsigned long long st[7];
         TC_CUDA_TRY(cudaMemcpyAsync(st, g->dev_scalars, sizeof(st), cudaMemcpyDeviceToHost, s));
         TC_CUDA_TRY(cudaStreamSynchronize(s));
+        if ((int64_t)st[6] != m) return fail(TC_ECUDA, "internal: oriented edge count mismatch");
         g->max_deg = (int32_t)st[0];
         g->max_out = (int32_t)st[1];
         for (int i = 0; i < 4; ++i) g->light_rows[i] = (int32_t)st[2 + i];

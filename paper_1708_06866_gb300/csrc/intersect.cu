@@ -393,6 +393,9 @@ __global__ void __launch_bounds__(IX_THREADS) k_edges_warp(
 #ifndef TC_CX_UNROLL
 #define TC_CX_UNROLL 4    // 32-wide chunks of a long segment in flight per warp pass
 #endif
+#ifndef TC_CX_SPLIT
+#define TC_CX_SPLIT 64    // long segments up to this length: two chunks per pass (0: off)
+#endif
 #ifndef TC_CX_MIN_BLOCKS
 #define TC_CX_MIN_BLOCKS 7  // resident blocks per SM the register allocation must allow (latency-bound: occupancy pays)
 #endif
@@ -429,6 +432,69 @@ struct ColArgs {
 
 __device__ __forceinline__ bool low_bit(const unsigned int* bits, int32_t e) {
     return (bits[e >> 5] >> (e & 31)) & 1u;
+}
+
+// One long segment of an in-neighbour u (edge ids [ss, se) of u's out-edges,
+// above v) streamed by the whole warp against column v's table, U chunks of
+// 32 entries in flight; returns this lane's hits (LISTS: entries read).
+template <int MODE, int U, typename P>
+__device__ __forceinline__ uint32_t stream_segment(const ColArgs& a, const int32_t* keys,
+                                                   const P* pos, int log_cap, int32_t* cnt,
+                                                   const unsigned int* sbase, int64_t ev,
+                                                   int32_t vmax, bool partial, int64_t ss,
+                                                   int64_t se, int32_t suv, bool sluv) {
+    const int lane = threadIdx.x & 31;
+    uint32_t c = 0;
+    for (int64_t cb = ss; cb < se; cb += 32 * U) {
+        int32_t w[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int64_t p = cb + 32 * q + lane;
+            w[q] = p < se ? a.head[p] : INT_MAX;
+            if (MODE == LISTS) c += p < se;  // LISTS counts the entries read
+        }
+        // segments ascend: once a chunk starts above max N+(v), nothing later matches
+        if (__shfl_sync(0xffffffffu, w[0], 0) > vmax) break;
+        int h[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+            h[q] = w[q] <= vmax ? table_find(keys, log_cap, w[q]) : -1;
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int64_t p = cb + 32 * q + lane;
+            if (MODE == LISTS) {
+                // the chunk's triangles share (u, v): one top append for all
+                const unsigned msk = __ballot_sync(0xffffffffu, h[q] >= 0);
+                if (msk) {
+                    const int ldr = __ffs(msk) - 1;
+                    unsigned base = 0;
+                    if (lane == ldr && sluv)
+                        base = atomicSub(&a.top[suv], (unsigned)__popc(msk));
+                    base = __shfl_sync(0xffffffffu, base, ldr) - (unsigned)__popc(msk);
+                    if (h[q] >= 0) {
+                        const int iw = pos[h[q]];
+                        const int32_t e_vw = (int32_t)(ev + iw), e_uw = (int32_t)p;
+                        if (sluv)
+                            a.pairs[base + __popc(msk & lanemask_lt())] =
+                                make_int2(e_uw, e_vw);
+                        if (!partial || low_bit(a.lowbits, e_uw))
+                            a.pairs[atomicSub(&a.top[e_uw], 1u) - 1u] = make_int2(suv, e_vw);
+                        if (sbase[iw] != 0xffffffffu)
+                            a.pairs[sbase[iw] + atomicAdd((unsigned int*)&cnt[iw], 1u)] =
+                                make_int2(suv, e_uw);
+                    }
+                }
+            }
+            if (h[q] >= 0) {
+                if (MODE != LISTS) ++c;
+                if (MODE == SUPPORT) {  // (v, w) on the column's counter, (u, w) = edge p
+                    atomicAdd(&cnt[pos[h[q]]], 1);
+                    atomicAdd(&a.sup[p], 1);
+                }
+            }
+        }
+    }
+    return c;
 }
 
 // One column's in-neighbours [i0, i1), in batches of 32 per warp; returns
@@ -491,53 +557,14 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
             const int64_t se = __shfl_sync(0xffffffffu, end, src);
             const int32_t suv = __shfl_sync(0xffffffffu, e_uv, src);
             const bool sluv = __shfl_sync(0xffffffffu, luv, src);
-            uint32_t c = 0;
-            for (int64_t cb = ss; cb < se; cb += 32 * TC_CX_UNROLL) {
-                int32_t w[TC_CX_UNROLL];
-#pragma unroll
-                for (int q = 0; q < TC_CX_UNROLL; ++q) {
-                    const int64_t p = cb + 32 * q + lane;
-                    w[q] = p < se ? a.head[p] : INT_MAX;
-                    if (MODE == LISTS) c += p < se;  // LISTS counts the entries read
-                }
-                // segments ascend: once a chunk starts above max N+(v), nothing later matches
-                if (__shfl_sync(0xffffffffu, w[0], 0) > vmax) break;
-                int h[TC_CX_UNROLL];
-#pragma unroll
-                for (int q = 0; q < TC_CX_UNROLL; ++q)
-                    h[q] = w[q] <= vmax ? table_find(keys, log_cap, w[q]) : -1;
-#pragma unroll
-                for (int q = 0; q < TC_CX_UNROLL; ++q) {
-                    const int64_t p = cb + 32 * q + lane;
-                    if (MODE == LISTS) {
-                        // the chunk's triangles share (u, v): one top append for all
-                        const unsigned msk = __ballot_sync(0xffffffffu, h[q] >= 0);
-                        if (msk) {
-                            const int ldr = __ffs(msk) - 1;
-                            unsigned base = 0;
-                            if (lane == ldr && sluv)
-                                base = atomicSub(&a.top[suv], (unsigned)__popc(msk));
-                            base = __shfl_sync(0xffffffffu, base, ldr) - (unsigned)__popc(msk);
-                            if (h[q] >= 0) {
-                                const int iw = pos[h[q]];
-                                const int32_t e_vw = (int32_t)(ev + iw), e_uw = (int32_t)p;
-                                if (sluv)
-                                    a.pairs[base + __popc(msk & lanemask_lt())] =
-                                        make_int2(e_uw, e_vw);
-                                if (!partial || low_bit(a.lowbits, e_uw))
-                                    a.pairs[atomicSub(&a.top[e_uw], 1u) - 1u] = make_int2(suv, e_vw);
-                                if (sbase[iw] != 0xffffffffu)
-                                    a.pairs[sbase[iw] + atomicAdd((unsigned int*)&cnt[iw], 1u)] =
-                                        make_int2(suv, e_uw);
-                            }
-                        }
-                    }
-                    if (h[q] >= 0) {
-                        if (MODE != LISTS) ++c;
-                        if (MODE == SUPPORT) hit_support(h[q], p);
-                    }
-                }
-            }
+            // segments up to TC_CX_SPLIT entries: two chunks per pass (fewer idle
+            // lanes in their one pass); longer ones TC_CX_UNROLL (more loads in flight)
+            uint32_t c = (TC_CX_SPLIT > 0 && se - ss <= TC_CX_SPLIT)
+                             ? stream_segment<MODE, 2>(a, keys, pos, log_cap, cnt, sbase, ev, vmax,
+                                                       partial, ss, se, suv, sluv)
+                             : stream_segment<MODE, TC_CX_UNROLL>(a, keys, pos, log_cap, cnt, sbase,
+                                                                   ev, vmax, partial, ss, se, suv,
+                                                                   sluv);
             c = warp_sum(c);
             if (lane == 0) {
                 acc += c;
