@@ -399,6 +399,11 @@ __global__ void __launch_bounds__(IX_THREADS) k_edges_warp(
 #ifndef TC_CX_MIN_BLOCKS
 #define TC_CX_MIN_BLOCKS 7  // resident blocks per SM the register allocation must allow (latency-bound: occupancy pays)
 #endif
+#ifndef TC_CX_LISTS_MIN_BLOCKS
+// the list build keeps more live state per entry; its shared-memory use caps it
+// at 6 blocks per SM anyway, so it takes the registers of 6 (no spills)
+#define TC_CX_LISTS_MIN_BLOCKS 6
+#endif
 #ifndef TC_CX_DYNAMIC
 #define TC_CX_DYNAMIC 1     // heavy columns: in-neighbour batches handed out dynamically
 #endif
@@ -441,17 +446,24 @@ template <int MODE, int U, typename P>
 __device__ __forceinline__ uint32_t stream_segment(const ColArgs& a, const int32_t* keys,
                                                    const P* pos, int log_cap, int32_t* cnt,
                                                    const unsigned int* sbase, int64_t ev,
-                                                   int32_t vmax, bool partial, int64_t ss,
-                                                   int64_t se, int32_t suv, bool sluv) {
+                                                   int32_t vmax, bool partial, int32_t ss,
+                                                   int32_t se, int32_t suv, bool sluv) {
+    // edge ids (below 2^31) index the segment: 32-bit arithmetic throughout
     const int lane = threadIdx.x & 31;
     uint32_t c = 0;
-    for (int64_t cb = ss; cb < se; cb += 32 * U) {
+    for (int32_t cb = ss; cb < se; cb += 32 * U) {
         int32_t w[U];
+        if (cb + 32 * U <= se) {  // a full pass: no bounds checks
 #pragma unroll
-        for (int q = 0; q < U; ++q) {
-            const int64_t p = cb + 32 * q + lane;
-            w[q] = p < se ? a.head[p] : INT_MAX;
-            if (MODE == LISTS) c += p < se;  // LISTS counts the entries read
+            for (int q = 0; q < U; ++q) w[q] = a.head[cb + 32 * q + lane];
+            if (MODE == LISTS) c += 32 * U;  // LISTS counts the entries read
+        } else {
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                const int32_t p = cb + 32 * q + lane;
+                w[q] = p < se ? a.head[p] : INT_MAX;
+                if (MODE == LISTS) c += p < se;
+            }
         }
         // segments ascend: once a chunk starts above max N+(v), nothing later matches
         if (__shfl_sync(0xffffffffu, w[0], 0) > vmax) break;
@@ -461,7 +473,7 @@ __device__ __forceinline__ uint32_t stream_segment(const ColArgs& a, const int32
             h[q] = w[q] <= vmax ? table_find(keys, log_cap, w[q]) : -1;
 #pragma unroll
         for (int q = 0; q < U; ++q) {
-            const int64_t p = cb + 32 * q + lane;
+            const int32_t p = cb + 32 * q + lane;
             if (MODE == LISTS) {
                 // the chunk's triangles share (u, v): one top append for all
                 const unsigned msk = __ballot_sync(0xffffffffu, h[q] >= 0);
@@ -561,10 +573,10 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
             // lanes in their one pass); longer ones TC_CX_UNROLL (more loads in flight)
             uint32_t c = (TC_CX_SPLIT > 0 && se - ss <= TC_CX_SPLIT)
                              ? stream_segment<MODE, 2>(a, keys, pos, log_cap, cnt, sbase, ev, vmax,
-                                                       partial, ss, se, suv, sluv)
+                                                       partial, (int32_t)ss, (int32_t)se, suv, sluv)
                              : stream_segment<MODE, TC_CX_UNROLL>(a, keys, pos, log_cap, cnt, sbase,
-                                                                   ev, vmax, partial, ss, se, suv,
-                                                                   sluv);
+                                                                   ev, vmax, partial, (int32_t)ss,
+                                                                   (int32_t)se, suv, sluv);
             c = warp_sum(c);
             if (lane == 0) {
                 acc += c;
@@ -622,7 +634,8 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(RX_THREADS, TC_CX_MIN_BLOCKS) k_cols(ColArgs a) {
+__global__ void __launch_bounds__(RX_THREADS, MODE == LISTS ? TC_CX_LISTS_MIN_BLOCKS : TC_CX_MIN_BLOCKS)
+    k_cols(ColArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_col;
     __shared__ unsigned int s_next;  // heavy column: next in-neighbour batch (offset)
