@@ -404,6 +404,12 @@ __global__ void __launch_bounds__(IX_THREADS) k_edges_warp(
 // at 6 blocks per SM anyway, so it takes the registers of 6 (no spills)
 #define TC_CX_LISTS_MIN_BLOCKS 6
 #endif
+#ifndef TC_CX_FULL_TABLE
+#define TC_CX_FULL_TABLE 1  // heavy columns: the whole table, whatever the column's size
+#endif
+#ifndef TC_CX_BITS
+#define TC_CX_BITS 1  // heavy columns spanning <= 32 x table slots of ranks: a bitmap
+#endif
 #ifndef TC_CX_DYNAMIC
 #define TC_CX_DYNAMIC 1     // heavy columns: in-neighbour batches handed out dynamically
 #endif
@@ -439,12 +445,97 @@ __device__ __forceinline__ bool low_bit(const unsigned int* bits, int32_t e) {
     return (bits[e >> 5] >> (e & 31)) & 1u;
 }
 
+// The list build's table: buckets of 4 slots (16 bytes, one shared-memory
+// load), linear probing by bucket.  A bucket fills from its first slot on
+// (an insert tries slot j only after slot j - 1 is taken), so a lookup ends
+// at the first bucket that holds w or has a free last slot.  At a load of
+// at most 1/4 (1/2 above 1024 entries) a bucket is rarely full: nearly every
+// lookup is one load, and a warp seldom waits on a lane's longer probe run.
+// (The support and count passes keep one slot per probe: there the 16-byte
+// loads' extra shared-memory wavefronts cost more than the probe runs.)
+__device__ __forceinline__ uint32_t bucket_of(int32_t w, int log_nb) {
+    return ((uint32_t)w * 0x9E3779B1u) >> (32 - log_nb);
+}
+
+__device__ __forceinline__ int table4_find(const int32_t* keys, int log_cap, int32_t w) {
+    const int log_nb = log_cap - 2;
+    const uint32_t bmask = (1u << log_nb) - 1;
+    uint32_t b = bucket_of(w, log_nb);
+    for (;;) {
+        const int4 k = reinterpret_cast<const int4*>(keys)[b];
+        const int j = k.x == w ? 0 : k.y == w ? 1 : k.z == w ? 2 : k.w == w ? 3 : -1;
+        if (j >= 0) return (int)(4 * b) + j;
+        if (k.w == -1) return -1;
+        b = (b + 1) & bmask;
+    }
+}
+
+// Inserts w (not yet present) and returns its slot.
+__device__ __forceinline__ int table4_insert(int32_t* keys, int log_cap, int32_t w) {
+    const int log_nb = log_cap - 2;
+    const uint32_t bmask = (1u << log_nb) - 1;
+    uint32_t b = bucket_of(w, log_nb);
+    for (;;) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (atomicCAS(&keys[4 * b + j], -1, w) == -1) return (int)(4 * b) + j;
+        b = (b + 1) & bmask;
+    }
+}
+
+// The column kernel's table by mode: LISTS buckets, the others single slots.
+template <int MODE>
+__device__ __forceinline__ int col_find(const int32_t* keys, int log_cap, int32_t w) {
+    return MODE == LISTS ? table4_find(keys, log_cap, w) : table_find(keys, log_cap, w);
+}
+
+template <int MODE>
+__device__ __forceinline__ int col_insert(int32_t* keys, int log_cap, int32_t w) {
+    if (MODE == LISTS) return table4_insert(keys, log_cap, w);
+    const uint32_t mask = (1u << log_cap) - 1;
+    uint32_t h = slot_of(w, log_cap);
+    while (atomicCAS(&keys[h], -1, w) != -1) h = (h + 1) & mask;
+    return (int)h;
+}
+
+// Column v's out-list N+(v) as the streaming loops see it: find(w) is w's
+// position in N+(v), or -1.  Callers pass only w with v < w <= max N+(v).
+// HashTab: the hash table above, with each slot's position beside it.
+template <typename P>
+struct HashTab {
+    const int32_t* keys;
+    const P* pos;
+    int log_cap;
+    template <int MODE>
+    __device__ __forceinline__ int find(int32_t w) const {
+        const int h = col_find<MODE>(keys, log_cap, w);
+        return h >= 0 ? (int)pos[h] : -1;
+    }
+};
+
+// BitTab: one bit per rank in (v, max N+(v)] (bit w - v - 1), for columns
+// whose out-list spans few enough ranks (the bits fit where the hash table's
+// keys would be).  A probe is one 4-byte shared-memory load with no probe
+// run.  pre[j] is the position in N+(v) of the first entry in word j (set
+// only for words that hold one), so a set bit's position is pre[j] plus the
+// set bits below it in its word.
+struct BitTab {
+    const uint32_t* bits;
+    const uint16_t* pre;
+    int32_t v;
+    template <int MODE>
+    __device__ __forceinline__ int find(int32_t w) const {
+        const uint32_t b = (uint32_t)(w - v - 1);
+        const uint32_t word = bits[b >> 5], bit = 1u << (b & 31);
+        return (word & bit) ? (int)pre[b >> 5] + __popc(word & (bit - 1u)) : -1;
+    }
+};
+
 // One long segment of an in-neighbour u (edge ids [ss, se) of u's out-edges,
 // above v) streamed by the whole warp against column v's table, U chunks of
 // 32 entries in flight; returns this lane's hits (LISTS: entries read).
-template <int MODE, int U, typename P>
-__device__ __forceinline__ uint32_t stream_segment(const ColArgs& a, const int32_t* keys,
-                                                   const P* pos, int log_cap, int32_t* cnt,
+template <int MODE, int U, typename Tab>
+__device__ __forceinline__ uint32_t stream_segment(const ColArgs& a, const Tab& t, int32_t* cnt,
                                                    const unsigned int* sbase, int64_t ev,
                                                    int32_t vmax, bool partial, int32_t ss,
                                                    int32_t se, int32_t suv, bool sluv) {
@@ -470,7 +561,7 @@ __device__ __forceinline__ uint32_t stream_segment(const ColArgs& a, const int32
         int h[U];
 #pragma unroll
         for (int q = 0; q < U; ++q)
-            h[q] = w[q] <= vmax ? table_find(keys, log_cap, w[q]) : -1;
+            h[q] = w[q] <= vmax ? t.template find<MODE>(w[q]) : -1;  // position in N+(v)
 #pragma unroll
         for (int q = 0; q < U; ++q) {
             const int32_t p = cb + 32 * q + lane;
@@ -484,7 +575,7 @@ __device__ __forceinline__ uint32_t stream_segment(const ColArgs& a, const int32
                         base = atomicSub(&a.top[suv], (unsigned)__popc(msk));
                     base = __shfl_sync(0xffffffffu, base, ldr) - (unsigned)__popc(msk);
                     if (h[q] >= 0) {
-                        const int iw = pos[h[q]];
+                        const int iw = h[q];
                         const int32_t e_vw = (int32_t)(ev + iw), e_uw = (int32_t)p;
                         if (sluv)
                             a.pairs[base + __popc(msk & lanemask_lt())] =
@@ -500,7 +591,7 @@ __device__ __forceinline__ uint32_t stream_segment(const ColArgs& a, const int32
             if (h[q] >= 0) {
                 if (MODE != LISTS) ++c;
                 if (MODE == SUPPORT) {  // (v, w) on the column's counter, (u, w) = edge p
-                    atomicAdd(&cnt[pos[h[q]]], 1);
+                    atomicAdd(&cnt[h[q]], 1);
                     atomicAdd(&a.sup[p], 1);
                 }
             }
@@ -511,10 +602,9 @@ __device__ __forceinline__ uint32_t stream_segment(const ColArgs& a, const int32
 
 // One column's in-neighbours [i0, i1), in batches of 32 per warp; returns
 // the triangles found (LISTS: the 4-byte words of out-lists read instead).
-// P: table position type.
-template <int MODE, typename P>
-__device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const int32_t* keys,
-                                                       const P* pos, int log_cap, int32_t* cnt,
+// Tab: column v's out-list (HashTab or BitTab).
+template <int MODE, typename Tab>
+__device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const Tab& t, int32_t* cnt,
                                                        const unsigned int* sbase, int64_t ev,
                                                        int32_t vmax, bool col_low, int64_t i0,
                                                        int64_t i1, unsigned int* next,
@@ -540,24 +630,23 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
     };
     for (int64_t ib = take(i0); ib < i1; ib = take(ib + stride)) {
         const int64_t i = lane < bsz ? ib + lane : i1;  // lanes past the batch: none
-        int64_t s = 0, end = 0;
+        int32_t s = 0, end = 0;  // edge ids: below 2^31
         int32_t e_uv = 0;
         bool luv = true;   // (u, v) has a list
         bool full = true;  // the whole segment is streamed
         if (i < i1) {
             e_uv = a.eid[i];
-            s = (int64_t)e_uv + 1;        // u's out-edges after (u, v), by edge id
+            s = e_uv + 1;                 // u's out-edges after (u, v), by edge id
             end = a.iend[i - ev];         // in-entries of column v start at index rowptr[v] - ev
             if (partial) {
                 luv = low_bit(a.lowbits, e_uv);
                 full = luv || col_low;
             }
         }
-        const int64_t len = full ? end - s : 0;
-        // a triangle (u, v, w) found at N+(u) position p, slot h
-        // a triangle (u, v, w): w at edge id q of u's out-edges, table slot h
-        auto hit_support = [&](int h, int64_t q) {
-            atomicAdd(&cnt[pos[h]], 1);
+        const int32_t len = full ? end - s : 0;
+        // a triangle (u, v, w): w at edge id q of u's out-edges, position h of N+(v)
+        auto hit_support = [&](int h, int32_t q) {
+            atomicAdd(&cnt[h], 1);
             atomicAdd(&a.sup[q], 1);
         };
         // long segments: the whole warp, one after another
@@ -565,19 +654,18 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
         while (lng) {
             const int src = __ffs(lng) - 1;
             lng &= lng - 1;
-            const int64_t ss = __shfl_sync(0xffffffffu, s, src);
-            const int64_t se = __shfl_sync(0xffffffffu, end, src);
+            const int32_t ss = __shfl_sync(0xffffffffu, s, src);
+            const int32_t se = __shfl_sync(0xffffffffu, end, src);
             const int32_t suv = __shfl_sync(0xffffffffu, e_uv, src);
             const bool sluv = __shfl_sync(0xffffffffu, luv, src);
             // segments up to TC_CX_SPLIT entries: two chunks per pass (fewer idle
             // lanes in their one pass); longer ones TC_CX_UNROLL (more loads in flight)
             uint32_t c = (TC_CX_SPLIT > 0 && se - ss <= TC_CX_SPLIT)
-                             ? stream_segment<MODE, 2>(a, keys, pos, log_cap, cnt, sbase, ev, vmax,
-                                                       partial, (int32_t)ss, (int32_t)se, suv, sluv)
-                             : stream_segment<MODE, TC_CX_UNROLL>(a, keys, pos, log_cap, cnt, sbase,
-                                                                   ev, vmax, partial, (int32_t)ss,
-                                                                   (int32_t)se, suv, sluv);
-            c = warp_sum(c);
+                             ? stream_segment<MODE, 2>(a, t, cnt, sbase, ev, vmax, partial, ss,
+                                                       se, suv, sluv)
+                             : stream_segment<MODE, TC_CX_UNROLL>(a, t, cnt, sbase, ev, vmax,
+                                                                   partial, ss, se, suv, sluv);
+            c = __reduce_add_sync(0xffffffffu, c);
             if (lane == 0) {
                 acc += c;
                 if (MODE == SUPPORT && c) atomicAdd(&a.sup[suv], (int)c);
@@ -586,20 +674,20 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
         // short segments: one lane each, four entries in flight
         if (len > 0 && len <= TC_CX_SHORT) {
             uint32_t c = 0;
-            for (int64_t p = s; p < end; p += 4) {
+            for (int32_t p = s; p < end; p += 4) {
                 int32_t w[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) w[q] = p + q < end ? a.head[p + q] : INT_MAX;
-                if (MODE == LISTS) c += (uint32_t)min((int64_t)4, end - p);
+                if (MODE == LISTS) c += (uint32_t)min(4, end - p);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     if (w[q] > vmax) continue;
-                    const int h = table_find(keys, log_cap, w[q]);
+                    const int h = t.template find<MODE>(w[q]);  // position in N+(v)
                     if (h < 0) continue;
                     if (MODE != LISTS) ++c;
                     if (MODE == SUPPORT) hit_support(h, p + q);
                     if (MODE == LISTS) {
-                        const int iw = pos[h];
+                        const int iw = h;
                         const int32_t e_vw = (int32_t)(ev + iw), e_uw = (int32_t)(p + q);
                         if (luv) a.pairs[atomicSub(&a.top[e_uv], 1u) - 1u] = make_int2(e_uw, e_vw);
                         if (!partial || low_bit(a.lowbits, e_uw))
@@ -623,9 +711,9 @@ __device__ __forceinline__ unsigned long long col_walk(const ColArgs& a, const i
                 const int2 we = a.lowlist[q];  // {w, edge id of (u, w)}
                 acc += 2;                      // an 8-byte entry read
                 if (we.x > vmax) break;
-                const int h = table_find(keys, log_cap, we.x);
+                const int h = t.template find<MODE>(we.x);
                 if (h < 0) continue;
-                const int32_t e_vw = (int32_t)(ev + pos[h]);
+                const int32_t e_vw = (int32_t)(ev + h);
                 a.pairs[atomicSub(&a.top[we.y], 1u) - 1u] = make_int2(e_uv, e_vw);
             }
         }
@@ -665,7 +753,10 @@ __global__ void __launch_bounds__(RX_THREADS, MODE == LISTS ? TC_CX_LISTS_MIN_BL
             const int dv = (int)(b1 - b0);
             if (dv < 1 || b0 == i0) continue;  // no out-list or no in-neighbour: no triangle
             const int64_t ev = b0 - a.oshift[v];  // first out-edge id of v
-            const int log_cap = min(table_log_cap(dv), a.max_log_cap);
+            // the block's table is sized for the largest column: a smaller
+            // column may use all of it (lower load, shorter probe runs)
+            const int log_cap = TC_CX_FULL_TABLE ? a.max_log_cap
+                                                 : min(table_log_cap(dv), a.max_log_cap);
             const int cap = 1 << log_cap;
             for (int i = threadIdx.x; i < cap; i += RX_THREADS) keys[i] = -1;
             bool low = false;  // some edge (v, w) of the column has a list
@@ -679,20 +770,39 @@ __global__ void __launch_bounds__(RX_THREADS, MODE == LISTS ? TC_CX_LISTS_MIN_BL
                     }
                 }
             const bool col_low = __syncthreads_or(low) != 0;
-            for (int i = threadIdx.x; i < dv; i += RX_THREADS) {
-                const int32_t w = a.head[ev + i];
-                uint32_t h = slot_of(w, log_cap);
-                while (atomicCAS(&keys[h], -1, w) != -1) h = (h + 1) & (cap - 1);
-                pos[h] = (uint16_t)i;
-            }
-            __syncthreads();
             const int32_t vmax = a.head[ev + dv - 1];
-            if (TC_CX_DYNAMIC)
-                acc += col_walk<MODE>(a, keys, pos, log_cap, cnt, sbase, ev, vmax, col_low, i0, b0,
-                                      &s_next);
-            else
-                acc += col_walk<MODE>(a, keys, pos, log_cap, cnt, sbase, ev, vmax, col_low,
-                                      i0 + 32 * warp, b0, nullptr, 32 * RX_WARPS);
+            // an out-list within 32 x cap ranks above v: a bitmap of those
+            // ranks in the keys' space, first positions per word in pos's
+            const int64_t span = (int64_t)vmax - v;  // bits 0 .. span - 1
+            if (TC_CX_BITS && MODE != LISTS && span <= 32 * (int64_t)max_cap) {
+                uint32_t* bits = reinterpret_cast<uint32_t*>(keys);
+                const int nw = (int)((span + 31) >> 5);
+                for (int i = threadIdx.x; i < nw; i += RX_THREADS) bits[i] = 0u;
+                __syncthreads();
+                for (int i = threadIdx.x; i < dv; i += RX_THREADS) {
+                    const uint32_t b = (uint32_t)(a.head[ev + i] - v - 1);
+                    atomicOr(&bits[b >> 5], 1u << (b & 31));
+                    if (i == 0 || (uint32_t)(a.head[ev + i - 1] - v - 1) >> 5 != b >> 5)
+                        pos[b >> 5] = (uint16_t)i;  // N+(v) ascends: i is the word's first
+                }
+                __syncthreads();
+                const BitTab t{bits, pos, v};
+                if (TC_CX_DYNAMIC)
+                    acc += col_walk<MODE>(a, t, cnt, sbase, ev, vmax, col_low, i0, b0, &s_next);
+                else
+                    acc += col_walk<MODE>(a, t, cnt, sbase, ev, vmax, col_low, i0 + 32 * warp, b0,
+                                          nullptr, 32 * RX_WARPS);
+            } else {
+                for (int i = threadIdx.x; i < dv; i += RX_THREADS)
+                    pos[col_insert<MODE>(keys, log_cap, a.head[ev + i])] = (uint16_t)i;
+                __syncthreads();
+                const HashTab<uint16_t> t{keys, pos, log_cap};
+                if (TC_CX_DYNAMIC)
+                    acc += col_walk<MODE>(a, t, cnt, sbase, ev, vmax, col_low, i0, b0, &s_next);
+                else
+                    acc += col_walk<MODE>(a, t, cnt, sbase, ev, vmax, col_low, i0 + 32 * warp, b0,
+                                          nullptr, 32 * RX_WARPS);
+            }
             __syncthreads();
             if (MODE == SUPPORT)
                 for (int i = threadIdx.x; i < dv; i += RX_THREADS)
@@ -741,16 +851,12 @@ __global__ void __launch_bounds__(RX_THREADS, MODE == LISTS ? TC_CX_LISTS_MIN_BL
                     }
                 const bool col_low = __any_sync(0xffffffffu, low);
                 __syncwarp();
-                for (int i = lane; i < dv; i += 32) {
-                    const int32_t w = a.head[ev + i];
-                    uint32_t h = slot_of(w, CX_LIGHT_LOG_CAP);
-                    while (atomicCAS(&keys[h], -1, w) != -1) h = (h + 1) & (CX_LIGHT_CAP - 1);
-                    pos[h] = (uint8_t)i;
-                }
+                for (int i = lane; i < dv; i += 32)
+                    pos[col_insert<MODE>(keys, CX_LIGHT_LOG_CAP, a.head[ev + i])] = (uint8_t)i;
                 __syncwarp();
                 const int32_t vmax = a.head[ev + dv - 1];
-                acc += col_walk<MODE>(a, keys, pos, CX_LIGHT_LOG_CAP, cnt, sbase, ev, vmax, col_low,
-                                      i0, b0, nullptr, 32);
+                const HashTab<uint8_t> t{keys, pos, CX_LIGHT_LOG_CAP};
+                acc += col_walk<MODE>(a, t, cnt, sbase, ev, vmax, col_low, i0, b0, nullptr, 32);
                 __syncwarp();
                 if (MODE == SUPPORT)
                     for (int i = lane; i < dv; i += 32)
