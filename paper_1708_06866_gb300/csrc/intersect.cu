@@ -774,7 +774,7 @@ __global__ void __launch_bounds__(RX_THREADS, MODE == LISTS ? TC_CX_LISTS_MIN_BL
             // an out-list within 32 x cap ranks above v: a bitmap of those
             // ranks in the keys' space, first positions per word in pos's
             const int64_t span = (int64_t)vmax - v;  // bits 0 .. span - 1
-            if (TC_CX_BITS && MODE != LISTS && span <= 32 * (int64_t)max_cap) {
+            if (TC_CX_BITS && span <= 32 * (int64_t)max_cap) {
                 uint32_t* bits = reinterpret_cast<uint32_t*>(keys);
                 const int nw = (int)((span + 31) >> 5);
                 for (int i = threadIdx.x; i < nw; i += RX_THREADS) bits[i] = 0u;
