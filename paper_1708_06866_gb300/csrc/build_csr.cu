@@ -228,12 +228,18 @@ __global__ void k_out_degree(const int64_t* __restrict__ rowptr, const int64_t* 
 // Internal ids number the out-entries in CSR order: the first out-edge of
 // row r is edge obase[r] (the out-degrees before r), so entry p is edge
 // p - (upper[r] - obase[r]).
+// oshift[r] = upper[r] - obase[r]; oend[r] = obase[r + 1], the end of r's
+// out-edge ids, as int32 (edge ids are below 2^31): a quarter of the bytes of
+// the two int64 arrays it replaces in k_out_entries' scattered reads, so
+// that those reads mostly hit L2.
 __global__ void k_oshift(const int64_t* __restrict__ upper,
                          const unsigned long long* __restrict__ obase, int32_t n,
-                         int64_t* __restrict__ oshift) {
+                         int64_t* __restrict__ oshift, int32_t* __restrict__ oend) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride)
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
         oshift[r] = upper[r] - (int64_t)obase[r];
+        oend[r] = (int32_t)obase[r + 1];
+    }
 }
 
 // Internal edge ids, from the sorted (row, neighbour) keys of the symmetric
@@ -243,12 +249,12 @@ __global__ void k_oshift(const int64_t* __restrict__ upper,
 // the edge's ends (row, neighbour) and head (neighbour), and its own edge id;
 // an in-entry (neighbour u below the row v), the
 // (p - first out-edge id of v)-th in-entry overall, records u's out-edge
-// end rowptr[u + 1] - oshift[u] (the column kernel's segment end).  A second
+// end oend[u] (the column kernel's segment end).  A second
 // pass then gives in-entries their edge ids through inv.  (Internal ids
 // follow the oriented adjacency so that per-edge arrays are read with
 // locality; canonical ids are restored at the ABI boundary.)
 __global__ void k_out_entries(const uint64_t* __restrict__ keys, int32_t* __restrict__ eid,
-                              int64_t nnz, int bits, const int64_t* __restrict__ rowptr,
+                              int64_t nnz, int bits, const int32_t* __restrict__ oend,
                               const int64_t* __restrict__ upper,
                               const int64_t* __restrict__ oshift, int32_t* __restrict__ inv,
                               int2* __restrict__ ends, int32_t* __restrict__ head,
@@ -266,7 +272,7 @@ __global__ void k_out_entries(const uint64_t* __restrict__ keys, int32_t* __rest
             eid[p] = j;
         } else {
             const int64_t first = upper[r] - oshift[r];  // edge id of r's first out-entry
-            iend[p - first] = (int32_t)(rowptr[c + 1] - oshift[c]);
+            iend[p - first] = oend[c];
         }
     }
 }
@@ -391,6 +397,7 @@ int build_graph(Graph* g, const int32_t* src, const int32_t* dst, cudaStream_t s
         // out-edge numbering: the first out-edge of row r is edge obase[r]
         // (the out-degrees before r); obase[n] must be m
         unsigned long long* obase;
+        int32_t* oend;
         {
             int32_t* dout;
             TC_TRY(sc.alloc(&dout, n));
@@ -399,14 +406,15 @@ int build_graph(Graph* g, const int32_t* src, const int32_t* dst, cudaStream_t s
             TC_LAUNCH_CHECK("k_out_degree");
             TC_TRY(exclusive_scan_i32(dout, n, obase, sc, s));
             TC_TRY(dev_alloc_n(&g->oshift, n, s));
-            k_oshift<<<grid_for(n), 256, 0, s>>>(g->upper, obase, n, g->oshift);
+            TC_TRY(sc.alloc(&oend, n));
+            k_oshift<<<grid_for(n), 256, 0, s>>>(g->upper, obase, n, g->oshift, oend);
             TC_LAUNCH_CHECK("k_oshift");
         }
         TC_TRY(dev_alloc_n(&g->head, m, s));
         TC_TRY(dev_alloc_n(&g->iend, m, s));
         if (m > 0) {
             int32_t* eid = g->eid;  // canonical ids from the sort, internal ids after
-            k_out_entries<<<grid_for(nnz), 256, 0, s>>>(pkeys, eid, nnz, bits, g->rowptr, g->upper,
+            k_out_entries<<<grid_for(nnz), 256, 0, s>>>(pkeys, eid, nnz, bits, oend, g->upper,
                                                         g->oshift, g->inv, g->ends, g->head,
                                                         g->iend);
             TC_LAUNCH_CHECK("k_out_entries");
