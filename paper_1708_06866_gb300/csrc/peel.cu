@@ -69,6 +69,7 @@ struct PeelCtl {
     unsigned long long cntW[2];  // window-list appends, by level parity
     unsigned long long cntF[2];  // light-frontier appends, by round parity
     unsigned long long cntH[2];  // heavy-frontier appends, by round parity
+    unsigned long long cntZ;     // edges of support 0 removed by a level scan (monotonic)
     int minenc[3];               // per level (mod 3): INT_MAX - smallest alive support scanned
     int abort;                   // 1 = a barrier wait ran out of time
     int kmax;                    // decomposition result
@@ -450,7 +451,7 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
 
     unsigned long long baseA[2] = {0, 0}, baseW[2] = {0, 0}, baseF[2] = {0, 0},
-                       baseH[2] = {0, 0};
+                       baseH[2] = {0, 0}, baseZ = 0;
     int ai = 0, wi = 0, fi = 0;  // which buffer of each pair is the current one
     bool first = true;           // the first full scan reads every edge id
     int64_t nA = a.m;            // entries of the current alive list
@@ -496,7 +497,11 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
             // before any is used (the scan is bound by load latency)
             constexpr int SU = TC_PK_SCAN_UNROLL;
             const int64_t wstep = nwarps * 32 * SU;
-            unsigned long long cA = 0, cW = 0, cF = 0, cH = 0;
+            // An edge below the threshold with support 0 is in no live
+            // triangle: removing it lowers no other support, so it is stamped
+            // with the round number (removed in round r, as the frontier is)
+            // but joins no frontier list (counted in cZ instead).
+            unsigned long long cA = 0, cW = 0, cF = 0, cH = 0, cZ = 0;
             for (int64_t base = gwarp * 32 * SU; base < n_in; base += wstep) {
                 int32_t e[SU], te[SU], se[SU];
 #pragma unroll
@@ -513,7 +518,7 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
                 }
 #pragma unroll
                 for (int u = 0; u < SU; ++u) {
-                    bool alive = false, win = false, light = false, heavy = false;
+                    bool alive = false, win = false, light = false, heavy = false, zero = false;
                     if (e[u] >= 0) {
                         ++tl.scanned;
                         alive = te[u] == 0;
@@ -522,8 +527,9 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
                             win = se[u] < bound;
                             if (se[u] < thr) {
                                 a.t[e[u]] = -r;
-                                heavy = TL && is_heavy(list_range(a, e[u]));
-                                light = !heavy;
+                                zero = se[u] == 0;
+                                heavy = !zero && TL && is_heavy(list_range(a, e[u]));
+                                light = !zero && !heavy;
                             }
                         }
                     }
@@ -531,6 +537,7 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
                     cW += __popc(__ballot_sync(0xffffffffu, win));
                     cF += __popc(__ballot_sync(0xffffffffu, light));
                     cH += __popc(__ballot_sync(0xffffffffu, heavy));
+                    cZ += __popc(__ballot_sync(0xffffffffu, zero));
                 }
             }
             smin = __reduce_min_sync(0xffffffffu, smin);
@@ -541,6 +548,7 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
                 if (wantW && cW) rW = atomicAdd(&ctl->cntW[wp], cW);
                 if (cF) rF = atomicAdd(&ctl->cntF[pf], cF);
                 if (cH) rH = atomicAdd(&ctl->cntH[pf], cH);
+                if (cZ) atomicAdd(&ctl->cntZ, cZ);
             }
             rA = __shfl_sync(0xffffffffu, rA, 0) - baseA[pa];
             rW = __shfl_sync(0xffffffffu, rW, 0) - baseW[wp];
@@ -565,7 +573,8 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
                             const bool front = te[u] == -r;
                             alive = te[u] == 0 || front;
                             if (alive && wantW) win = ld_cg(a.s + e[u]) < bound;
-                            if (front) {
+                            // (the frontier leaves out edges of support 0)
+                            if (front && ld_cg(a.s + e[u]) > 0) {
                                 if (TL) rg = list_range(a, e[u]);
                                 heavy = TL && is_heavy(rg);
                                 light = !heavy;
@@ -621,6 +630,9 @@ __global__ void __launch_bounds__(PK_THREADS) k_peel(PeelArgs a) {
             nH = (int64_t)(eH - baseH[pf]);
             baseF[pf] = eF;
             baseH[pf] = eH;
+            const unsigned long long eZ = ld_vol(&ctl->cntZ);
+            n_alive -= (int64_t)(eZ - baseZ);  // support-0 edges: removed now
+            baseZ = eZ;
         }
         // no edge below the threshold: levels up to the smallest alive
         // support + 2 remove nothing either (their k-trusses are all alive
