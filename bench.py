@@ -48,7 +48,16 @@ CPU_SAMPLE_SCALE = 16   # oracle sample: the same R-MAT generator at scale 16
 # kernel's source file at capture time.  The bench reports the bytes only
 # while that file is unchanged (otherwise traffic is null: the counters no
 # longer describe the kernel that ran).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("rmat24", "masked product, support"): {
+        "bytes": 222134330368 + 67137693696,
+        "source": "profiles/k_cols_support_dram_rmat24.md (one launch, single-pass counters)",
+        "source_sha256": "47894031f0f4f1d9898cd78a39baf833158a1da92bee37dc6f5b175008a0ecc8"},
+    ("rmat22", "masked product, support"): {
+        "bytes": 20300904448 + 6242865920,
+        "source": "profiles/k_cols_support_dram_rmat24.md (one launch, single-pass counters)",
+        "source_sha256": "47894031f0f4f1d9898cd78a39baf833158a1da92bee37dc6f5b175008a0ecc8"},
+}
 
 KERNEL_SOURCE = {
     "masked product, count": "intersect.cu",
@@ -588,6 +597,10 @@ def bench_ours(args, rank, world):
     if tr is not None:
         roofline["traffic"] = tr["bytes"]
         roofline["traffic_source"] = tr["source"]
+        # the same launch time over the captured DRAM bytes: the kernel's
+        # actual DRAM rate against the same peak
+        roofline["traffic_frac"] = round(
+            tr["bytes"] / (dom["ms_per_launch"] * 1e6) / roofline["peak"], 4)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
