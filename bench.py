@@ -50,13 +50,13 @@ CPU_SAMPLE_SCALE = 16   # oracle sample: the same R-MAT generator at scale 16
 # longer describe the kernel that ran).
 NCU_TRAFFIC = {
     ("rmat24", "masked product, support"): {
-        "bytes": 222134330368 + 67137693696,
+        "bytes": 221641408768 + 66881868800,
         "source": "profiles/k_cols_support_dram_rmat24.md (one launch, single-pass counters)",
-        "source_sha256": "47894031f0f4f1d9898cd78a39baf833158a1da92bee37dc6f5b175008a0ecc8"},
+        "source_sha256": "e84d1da4c2ed54d34d39b2c3c1568109733ac360228972af1a18051c3df29040"},
     ("rmat22", "masked product, support"): {
-        "bytes": 20300904448 + 6242865920,
+        "bytes": 20330333952 + 6250090752,
         "source": "profiles/k_cols_support_dram_rmat24.md (one launch, single-pass counters)",
-        "source_sha256": "47894031f0f4f1d9898cd78a39baf833158a1da92bee37dc6f5b175008a0ecc8"},
+        "source_sha256": "e84d1da4c2ed54d34d39b2c3c1568109733ac360228972af1a18051c3df29040"},
 }
 
 KERNEL_SOURCE = {

@@ -547,7 +547,7 @@ __device__ __forceinline__ uint32_t stream_segment(const ColArgs& a, const Tab& 
         if (cb + 32 * U <= se) {  // a full pass: no bounds checks
 #pragma unroll
             for (int q = 0; q < U; ++q) w[q] = a.head[cb + 32 * q + lane];
-            if (MODE == LISTS) c += 32 * U;  // LISTS counts the entries read
+            if (MODE == LISTS) c += U;  // LISTS counts the entries read (this lane's)
         } else {
 #pragma unroll
             for (int q = 0; q < U; ++q) {

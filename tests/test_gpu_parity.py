@@ -450,6 +450,32 @@ def test_every_intersection_kernel_builds_the_same_lists():
             tc.tc_graph_free(g)
 
 
+def test_column_list_build_counts_the_words_it_reads():
+    """The column kernel's list build reports its algorithmic bytes from a
+    count of the out-list words it read.  Building every edge's list reads
+    each entry of N+(u) above v at most once per oriented edge (u, v), and
+    reads the entry w of every triangle u < v < w, so the count lies between
+    T and the column work (Section III-A's masked product by columns)."""
+    src, dst, n = graphgen.rmat(14, 16, seed=7)
+    og = oracle.OracleGraph.from_edges(src, dst, n)
+    T = og.count()
+    g = tc.tc_build_csr(dev(src), dev(dst), n)
+    tc.tc_graph_wedge_work(g)
+    pi = tc.tc_debug_intersect_mode(1)
+    pp = tc.tc_debug_peel_mode(PEEL_MODES["lists"])
+    try:
+        tc.ktruss_max(g)
+    finally:
+        tc.tc_debug_intersect_mode(pi)
+        tc.tc_debug_peel_mode(pp)
+    inf = tc.tc_graph_info(g)
+    rest = inf["lists_bytes"] - 24 * g.m - 24 * g.n - 16 * 3 * T
+    assert rest % 4 == 0
+    words = rest // 4
+    assert T <= words <= inf["column_work"], (T, words, inf["column_work"])
+    tc.tc_graph_free(g)
+
+
 def test_from_a_tab_separated_file(tmp_path):
     """The Graph Challenge's input path: a 1-based tab-separated file with
     both directions of every edge and unit weights (Section II), read by
