@@ -178,12 +178,6 @@ int build(tc_server* s, Slot& slot, int32_t gid) {
     const tc_graph_source& g = s->src[gid];
     TC_TRY(tc_build_csr(g.src, g.dst, g.m_in, g.n, TC_INPUT_HOST, slot.stream, &e.g));
     TC_TRY(tc_graph_set_result_cache(e.g, s->keep_results ? 1 : 0));
-#ifdef TC_SERVE_PEEL_DIV
-    e.g->g.peel_max_blocks = std::max(1, tc::num_sms() / TC_SERVE_PEEL_DIV);
-#endif
-#ifdef TC_SERVE_SMALL_M
-    if (g.m_in <= (int64_t)TC_SERVE_SMALL_M) e.g->g.peel_max_blocks = 1;
-#endif
     return tc_graph_set_memory_limit(e.g, s->opt_per_pair * g.m_in);
 }
 
