@@ -6,10 +6,12 @@
 //              DEV_ERR_RANGE.                                    (Section II)
 //   2. sort + dedupe -> the canonical edge list lo[e] < hi[e].
 //   3. degrees, and the degree order rank(v) = position of (deg(v), v).
-//   4. both directions of every edge in rank ids, sorted -> a symmetric CSR
-//      whose rows are ascending; the part of row u above u is N+(u), the
-//      out-list of the degree-oriented adjacency L (Algorithm 3's L with a
-//      degree order in place of the index order).
+//   4. every edge as (lower rank, higher rank), sorted -> the out-lists
+//      N+(u) of the degree-oriented adjacency L (Algorithm 3's L with a
+//      degree order in place of the index order), numbering the edges; the
+//      same pairs stably re-sorted by their higher end -> the in-lists.
+//      Together: a symmetric CSR whose rows ascend, each row's in-entries
+//      (below u) followed by N+(u).
 #include <algorithm>
 
 #include "tc_internal.cuh"
@@ -131,61 +133,120 @@ __global__ void k_rank(const uint64_t* __restrict__ sorted, int32_t n, int bits,
         rank[sorted[p] & mask] = (int32_t)p;
 }
 
-__global__ void k_pairs(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi, int64_t m,
-                        const int32_t* __restrict__ rank, int bits,
-                        uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+// One key per edge, oriented by rank: (lower rank u) << bits | (higher rank
+// v), with the edge's canonical id as its value.  Sorted, these are the
+// out-lists N+(u) in CSR order, and an edge's position in that order is its
+// internal id.
+__global__ void k_out_pairs(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                            int64_t m, const int32_t* __restrict__ rank, int bits,
+                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         const int32_t a = rank[lo[e]], c = rank[hi[e]];
-        const int32_t u = min(a, c), v = max(a, c);
-        keys[2 * e] = ((uint64_t)u << bits) | (uint64_t)v;
-        keys[2 * e + 1] = ((uint64_t)v << bits) | (uint64_t)u;
-        vals[2 * e] = (uint32_t)e;
-        vals[2 * e + 1] = (uint32_t)e;
+        keys[e] = ((uint64_t)min(a, c) << bits) | (uint64_t)max(a, c);
+        vals[e] = (uint32_t)e;
     }
 }
 
-// col from the sorted keys; row boundaries -> rowptr; first entry above the
-// row -> upper (rows with none keep upper = rowptr[r + 1], set beforehand).
-// col from the sorted (row, col) keys; rowptr[r] = first entry of row r.
-// Entry i sets the offsets of the rows from its predecessor's row + 1 to its
-// own.  The rows before the first entry (the degree-0 vertices, which the
-// degree order puts first — millions of them in a large R-MAT graph) are
-// set by a separate grid-stride loop, not by entry 0's thread alone.
-__global__ void k_csr_fill(const uint64_t* __restrict__ keys, int64_t nnz, int32_t n, int bits,
-                           int32_t* __restrict__ col, int64_t* __restrict__ rowptr) {
+// obase[r] = the first position of the sorted out-pairs whose row is >= r
+// (r = 0 .. n; obase[n] = m): the out-degrees' exclusive scan, read off the
+// sorted keys.  Entry i sets the rows from its predecessor's row + 1 to its
+// own; the rows before the first entry (the degree-0 vertices, which the
+// degree order puts first) are set by a grid-stride loop.
+__global__ void k_out_starts(const uint64_t* __restrict__ keys, int64_t m, int32_t n, int bits,
+                             unsigned long long* __restrict__ obase) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const uint64_t mask = (1ull << bits) - 1;
-    const int64_t first = nnz > 0 ? (int64_t)(keys[0] >> bits) : (int64_t)n;
-    for (int64_t r = tid; r <= first; r += stride) rowptr[r] = 0;
-    for (int64_t i = tid + 1; i <= nnz; i += stride) {
+    const int64_t first = m > 0 ? (int64_t)(keys[0] >> bits) : (int64_t)n;
+    for (int64_t r = tid; r <= first; r += stride) obase[r] = 0;
+    for (int64_t i = tid + 1; i <= m; i += stride) {
         const int64_t r_prev = (int64_t)(keys[i - 1] >> bits);
-        const int64_t r_cur = i == nnz ? (int64_t)n : (int64_t)(keys[i] >> bits);
-        for (int64_t r = r_prev + 1; r <= r_cur; ++r) rowptr[r] = i;
+        const int64_t r_cur = i == m ? (int64_t)n : (int64_t)(keys[i] >> bits);
+        for (int64_t r = r_prev + 1; r <= r_cur; ++r) obase[r] = (unsigned long long)i;
     }
-    for (int64_t i = tid; i < nnz; i += stride) col[i] = (int32_t)(keys[i] & mask);
 }
 
-__global__ void k_upper_init(const int64_t* __restrict__ rowptr, int32_t n,
-                             int64_t* __restrict__ upper) {
+// Degrees by rank (the symmetric CSR's row lengths).
+__global__ void k_rank_degrees(const int32_t* __restrict__ deg, const int32_t* __restrict__ rank,
+                               int32_t n, int32_t* __restrict__ deg_rank) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride)
-        upper[r] = rowptr[r + 1];
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride)
+        deg_rank[rank[x]] = deg[x];
 }
 
-__global__ void k_upper(const uint64_t* __restrict__ keys, int64_t nnz, int bits,
-                        int64_t* __restrict__ upper) {
+// Row r of the symmetric CSR holds its in-entries (neighbours below r) and
+// then its out-entries: upper[r] = rowptr[r] + in-degree; out-entry p of row
+// r is internal edge p - oshift[r] with oshift[r] = upper[r] - obase[r];
+// oend[r] = obase[r + 1] is the end of r's out-edge ids (int32: edge ids are
+// below 2^31; a small array, so the scattered reads of it mostly hit L2).
+__global__ void k_row_bounds(const int64_t* __restrict__ rowptr,
+                             const unsigned long long* __restrict__ obase,
+                             const int32_t* __restrict__ deg_rank, int32_t n,
+                             int64_t* __restrict__ upper, int64_t* __restrict__ oshift,
+                             int32_t* __restrict__ oend, int* __restrict__ err) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        const int64_t dout = (int64_t)(obase[r + 1] - obase[r]);
+        const int64_t din = (int64_t)deg_rank[r] - dout;
+        if (din < 0) atomicOr(err, DEV_ERR_BOUNDS);  // degrees and pairs disagree
+        upper[r] = rowptr[r] + din;
+        oshift[r] = upper[r] - (int64_t)obase[r];
+        oend[r] = (int32_t)obase[r + 1];
+    }
+}
+
+// Out-entries from the sorted out-pairs: internal edge j = (u, v) records
+// its ends, its head v, the inverse map inv[canonical id] = j, and its entry
+// at position j + oshift[u] of row u; vals[j] becomes j, the value the
+// in-entry sort carries.
+__global__ void k_out_part(const uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                           int64_t m, int bits, const int64_t* __restrict__ oshift,
+                           int32_t* __restrict__ inv, int2* __restrict__ ends,
+                           int32_t* __restrict__ head, int32_t* __restrict__ col,
+                           int32_t* __restrict__ eid, int* __restrict__ err) {
     const uint64_t mask = (1ull << bits) - 1;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += stride) {
-        const uint64_t k = keys[i];
-        const uint64_t row = k >> bits, c = k & mask;
-        if (c > row) {
-            const bool first = i == 0 || (keys[i - 1] >> bits) != row ||
-                                (keys[i - 1] & mask) < row;
-            if (first) upper[row] = i;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        const uint64_t k = keys[j];
+        const int32_t u = (int32_t)(k >> bits), v = (int32_t)(k & mask);
+        inv[vals[j]] = (int32_t)j;
+        vals[j] = (uint32_t)j;
+        ends[j] = make_int2(u, v);
+        head[j] = v;
+        const int64_t p = j + oshift[u];
+        if (p < 0 || p >= 2 * m) {  // only if degrees and pairs disagree
+            atomicOr(err, DEV_ERR_BOUNDS);
+            continue;
         }
+        col[p] = v;
+        eid[p] = (int32_t)j;
+    }
+}
+
+// In-entries from the out-pairs stably re-sorted by their higher end v: the
+// q-th of them is u's entry in row v (rows ascend by v, and within a row by
+// u, since the first order was by (u, v)), at position q + obase[v] (the
+// in-entries before row v number rowptr[v] - obase[v]); it records edge j,
+// and iend[q], the end of u's out-edge ids (the column kernel streams u's
+// out-list above v up to it).
+__global__ void k_in_part(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                          int64_t m, int bits, const unsigned long long* __restrict__ obase,
+                          const int32_t* __restrict__ oend, int32_t* __restrict__ col,
+                          int32_t* __restrict__ eid, int32_t* __restrict__ iend,
+                          int* __restrict__ err) {
+    const uint64_t mask = (1ull << bits) - 1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += stride) {
+        const uint64_t k = keys[q];
+        const int32_t u = (int32_t)(k >> bits), v = (int32_t)(k & mask);
+        const int64_t p = q + (int64_t)obase[v];
+        iend[q] = oend[u];
+        if (p >= 2 * m) {  // only if degrees and pairs disagree
+            atomicOr(err, DEV_ERR_BOUNDS);
+            continue;
+        }
+        col[p] = u;
+        eid[p] = (int32_t)vals[q];
     }
 }
 
@@ -215,75 +276,6 @@ __global__ void k_row_stats(const int64_t* __restrict__ rowptr, const int64_t* _
         atomicMax(&out[1], mo);
 #pragma unroll
         for (int i = 0; i < 4; ++i) atomicAdd(&out[2 + i], nl[i]);
-    }
-}
-
-__global__ void k_out_degree(const int64_t* __restrict__ rowptr, const int64_t* __restrict__ upper,
-                             int32_t n, int32_t* __restrict__ dout) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride)
-        dout[r] = (int32_t)(rowptr[r + 1] - upper[r]);
-}
-
-// Internal ids number the out-entries in CSR order: the first out-edge of
-// row r is edge obase[r] (the out-degrees before r), so entry p is edge
-// p - (upper[r] - obase[r]).
-// oshift[r] = upper[r] - obase[r]; oend[r] = obase[r + 1], the end of r's
-// out-edge ids, as int32 (edge ids are below 2^31): a quarter of the bytes of
-// the two int64 arrays it replaces in k_out_entries' scattered reads, so
-// that those reads mostly hit L2.
-__global__ void k_oshift(const int64_t* __restrict__ upper,
-                         const unsigned long long* __restrict__ obase, int32_t n,
-                         int64_t* __restrict__ oshift, int32_t* __restrict__ oend) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
-        oshift[r] = upper[r] - (int64_t)obase[r];
-        oend[r] = (int32_t)obase[r + 1];
-    }
-}
-
-// Internal edge ids, from the sorted (row, neighbour) keys of the symmetric
-// CSR and the canonical id each entry carries: an out-entry (neighbour above
-// the row) at position p is internal edge j = p - oshift[row] (a row's
-// out-edges are numbered consecutively), so it records inv[canonical] = j,
-// the edge's ends (row, neighbour) and head (neighbour), and its own edge id;
-// an in-entry (neighbour u below the row v), the
-// (p - first out-edge id of v)-th in-entry overall, records u's out-edge
-// end oend[u] (the column kernel's segment end).  A second
-// pass then gives in-entries their edge ids through inv.  (Internal ids
-// follow the oriented adjacency so that per-edge arrays are read with
-// locality; canonical ids are restored at the ABI boundary.)
-__global__ void k_out_entries(const uint64_t* __restrict__ keys, int32_t* __restrict__ eid,
-                              int64_t nnz, int bits, const int32_t* __restrict__ oend,
-                              const int64_t* __restrict__ upper,
-                              const int64_t* __restrict__ oshift, int32_t* __restrict__ inv,
-                              int2* __restrict__ ends, int32_t* __restrict__ head,
-                              int32_t* __restrict__ iend) {
-    const uint64_t mask = (1ull << bits) - 1;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
-        const uint64_t k = keys[p];
-        const int32_t r = (int32_t)(k >> bits), c = (int32_t)(k & mask);
-        if (c > r) {
-            const int32_t j = (int32_t)(p - oshift[r]);
-            inv[eid[p]] = j;
-            ends[j] = make_int2(r, c);
-            head[j] = c;
-            eid[p] = j;
-        } else {
-            const int64_t first = upper[r] - oshift[r];  // edge id of r's first out-entry
-            iend[p - first] = oend[c];
-        }
-    }
-}
-
-__global__ void k_in_entries(const uint64_t* __restrict__ keys, int32_t* __restrict__ eid,
-                             int64_t nnz, int bits, const int32_t* __restrict__ inv) {
-    const uint64_t mask = (1ull << bits) - 1;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
-        const uint64_t k = keys[p];
-        if ((int32_t)(k & mask) < (int32_t)(k >> bits)) eid[p] = inv[eid[p]];
     }
 }
 
@@ -374,62 +366,58 @@ int build_graph(Graph* g, const int32_t* src, const int32_t* dst, cudaStream_t s
         k_rank<<<grid_for(n), 256, 0, s>>>(vkeys, n, bits, rank);
         TC_LAUNCH_CHECK("k_rank");
 
-        const int64_t nnz = 2 * m;
+        // 4. the symmetric CSR in rank ids.  The out-pairs (u < v, one per
+        // edge) sorted by (u, v) are the out-lists, and their order numbers
+        // the edges; re-sorted stably by v alone (its digits only) they are
+        // the in-lists, already in row order.  Row lengths come from the
+        // degrees, so rows are laid out before either sort finishes.
         uint64_t *pkeys, *pkeys_alt;
         uint32_t *pvals, *pvals_alt;
-        TC_TRY(sc.alloc(&pkeys, nnz));
-        TC_TRY(sc.alloc(&pkeys_alt, nnz));
-        TC_TRY(sc.alloc(&pvals_alt, nnz));
-        pvals = reinterpret_cast<uint32_t*>(g->eid);
-        if (m > 0) {
-            k_pairs<<<grid_for(m), 256, 0, s>>>(g->lo, g->hi, m, rank, bits, pkeys, pvals);
-            TC_LAUNCH_CHECK("k_pairs");
-            TC_TRY(radix_sort_u64(pkeys, pkeys_alt, pvals, pvals_alt, nnz, 2 * bits, g->dev_err, s));
-        }
-        k_csr_fill<<<grid_for(nnz + 1), 256, 0, s>>>(pkeys, nnz, n, bits, g->col, g->rowptr);
-        TC_LAUNCH_CHECK("k_csr_fill");
-        k_upper_init<<<grid_for(n), 256, 0, s>>>(g->rowptr, n, g->upper);
-        TC_LAUNCH_CHECK("k_upper_init");
-        if (m > 0) {
-            k_upper<<<grid_for(nnz), 256, 0, s>>>(pkeys, nnz, bits, g->upper);
-            TC_LAUNCH_CHECK("k_upper");
-        }
-        // out-edge numbering: the first out-edge of row r is edge obase[r]
-        // (the out-degrees before r); obase[n] must be m
+        int32_t *deg_rank, *oend;
         unsigned long long* obase;
-        int32_t* oend;
-        {
-            int32_t* dout;
-            TC_TRY(sc.alloc(&dout, n));
-            TC_TRY(sc.alloc(&obase, (int64_t)n + 1));
-            k_out_degree<<<grid_for(n), 256, 0, s>>>(g->rowptr, g->upper, n, dout);
-            TC_LAUNCH_CHECK("k_out_degree");
-            TC_TRY(exclusive_scan_i32(dout, n, obase, sc, s));
-            TC_TRY(dev_alloc_n(&g->oshift, n, s));
-            TC_TRY(sc.alloc(&oend, n));
-            k_oshift<<<grid_for(n), 256, 0, s>>>(g->upper, obase, n, g->oshift, oend);
-            TC_LAUNCH_CHECK("k_oshift");
-        }
+        TC_TRY(sc.alloc(&pkeys, m));
+        TC_TRY(sc.alloc(&pkeys_alt, m));
+        TC_TRY(sc.alloc(&pvals, m));
+        TC_TRY(sc.alloc(&pvals_alt, m));
+        TC_TRY(sc.alloc(&deg_rank, n));
+        TC_TRY(sc.alloc(&obase, (int64_t)n + 1));
+        TC_TRY(sc.alloc(&oend, n));
+        TC_TRY(dev_alloc_n(&g->oshift, n, s));
         TC_TRY(dev_alloc_n(&g->head, m, s));
         TC_TRY(dev_alloc_n(&g->iend, m, s));
         if (m > 0) {
-            int32_t* eid = g->eid;  // canonical ids from the sort, internal ids after
-            k_out_entries<<<grid_for(nnz), 256, 0, s>>>(pkeys, eid, nnz, bits, oend, g->upper,
-                                                        g->oshift, g->inv, g->ends, g->head,
-                                                        g->iend);
-            TC_LAUNCH_CHECK("k_out_entries");
-            k_in_entries<<<grid_for(nnz), 256, 0, s>>>(pkeys, eid, nnz, bits, g->inv);
-            TC_LAUNCH_CHECK("k_in_entries");
+            k_out_pairs<<<grid_for(m), 256, 0, s>>>(g->lo, g->hi, m, rank, bits, pkeys, pvals);
+            TC_LAUNCH_CHECK("k_out_pairs");
+            TC_TRY(radix_sort_u64(pkeys, pkeys_alt, pvals, pvals_alt, m, 2 * bits, g->dev_err, s));
+        }
+        k_out_starts<<<grid_for(m + 1), 256, 0, s>>>(pkeys, m, n, bits, obase);
+        TC_LAUNCH_CHECK("k_out_starts");
+        k_rank_degrees<<<grid_for(n), 256, 0, s>>>(deg, rank, n, deg_rank);
+        TC_LAUNCH_CHECK("k_rank_degrees");
+        TC_TRY(exclusive_scan_i32(deg_rank, n, reinterpret_cast<unsigned long long*>(g->rowptr),
+                                  sc, s));
+        k_row_bounds<<<grid_for(n), 256, 0, s>>>(g->rowptr, obase, deg_rank, n, g->upper,
+                                                 g->oshift, oend, g->dev_err);
+        TC_LAUNCH_CHECK("k_row_bounds");
+        if (m > 0) {
+            k_out_part<<<grid_for(m), 256, 0, s>>>(pkeys, pvals, m, bits, g->oshift, g->inv,
+                                                   g->ends, g->head, g->col, g->eid, g->dev_err);
+            TC_LAUNCH_CHECK("k_out_part");
+            TC_TRY(radix_sort_u64(pkeys, pkeys_alt, pvals, pvals_alt, m, bits, g->dev_err, s));
+            k_in_part<<<grid_for(m), 256, 0, s>>>(pkeys, pvals, m, bits, obase, oend, g->col,
+                                                  g->eid, g->iend, g->dev_err);
+            TC_LAUNCH_CHECK("k_in_part");
         }
         TC_CUDA_TRY(cudaMemsetAsync(g->dev_scalars, 0, 6 * sizeof(unsigned long long), s));
         k_row_stats<<<grid_for(n), 256, 0, s>>>(g->rowptr, g->upper, n, g->dev_scalars);
         TC_LAUNCH_CHECK("k_row_stats");
-        TC_CUDA_TRY(cudaMemcpyAsync(g->dev_scalars + 6, obase + n, sizeof(unsigned long long),
+        // the degrees must sum to 2m (rowptr[n]), as the pairs do
+        TC_CUDA_TRY(cudaMemcpyAsync(g->dev_scalars + 6, g->rowptr + n, sizeof(unsigned long long),
                                     cudaMemcpyDeviceToDevice, s));
         unsigned long long st[7];
         TC_CUDA_TRY(cudaMemcpyAsync(st, g->dev_scalars, sizeof(st), cudaMemcpyDeviceToHost, s));
         TC_CUDA_TRY(cudaStreamSynchronize(s));
-        if ((int64_t)st[6] != m) return fail(TC_ECUDA, "internal: oriented edge count mismatch");
+        if ((int64_t)st[6] != 2 * m) return fail(TC_ECUDA, "internal: degree sum mismatch");
         g->max_deg = (int32_t)st[0];
         g->max_out = (int32_t)st[1];
         for (int i = 0; i < 4; ++i) g->light_rows[i] = (int32_t)st[2 + i];
