@@ -86,6 +86,20 @@ bool is_host_pointer(const void* p) {
     return a.type == cudaMemoryTypeUnregistered || a.type == cudaMemoryTypeHost;
 }
 
+// The device's address of host memory the GPU can reach directly (pinned or
+// registered memory, mapped into the device's address space), else nullptr
+// (pageable memory: the caller copies).  On a GB300's coherent host link a
+// kernel reads or writes such memory itself, so inputs and outputs in it
+// skip the separate copy pass.
+void* host_device_view(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int check_dev_err(int* dev_err, cudaStream_t s) {
     int h = 0;
     TC_CUDA_TRY(cudaMemcpyAsync(&h, dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -196,7 +210,14 @@ int tc_build_csr(const int32_t* src, const int32_t* dst, int64_t m_in, int32_t n
         const int32_t* sd = src;
         const int32_t* dd = dst;
         tc::Scratch sc(s);
-        if (host && m_in > 0) {
+        const int32_t* sv = host && m_in > 0 ? static_cast<const int32_t*>(tc::host_device_view(src))
+                                              : nullptr;
+        const int32_t* dv = host && m_in > 0 ? static_cast<const int32_t*>(tc::host_device_view(dst))
+                                              : nullptr;
+        if (sv && dv) {  // pinned input: the first kernel reads it in place
+            sd = sv;
+            dd = dv;
+        } else if (host && m_in > 0) {
             int32_t *s2 = nullptr, *d2 = nullptr;
             rc = sc.alloc(&s2, m_in);
             if (rc == TC_OK) rc = sc.alloc(&d2, m_in);
@@ -263,6 +284,11 @@ int tc_edge_support(tc_graph* g, int32_t* support_out, int64_t* triangles_out,
     if (gg->m == 0) return TC_OK;
     if (!tc::is_host_pointer(support_out))
         return tc::to_canonical_i32(gg->support, gg->inv, gg->m, support_out, s);
+    if (void* v = tc::host_device_view(support_out)) {  // pinned: written in place
+        TC_TRY(tc::to_canonical_i32(gg->support, gg->inv, gg->m, static_cast<int32_t*>(v), s));
+        TC_CUDA_TRY(cudaStreamSynchronize(s));
+        return TC_OK;
+    }
     tc::Scratch sc(s);
     int32_t* tmp;
     TC_TRY(sc.alloc(&tmp, gg->m));
@@ -277,10 +303,17 @@ int ktruss(tc_graph* g, int32_t k, uint8_t* mask_out, int64_t* edges_out, void* 
     if (!mask_out && gg->m > 0) return fail(TC_EINVAL, "mask_out is NULL");
     DeviceGuard dg(gg->device);
     cudaStream_t s = as_stream(cuda_stream);
-    const bool host = gg->m > 0 && tc::is_host_pointer(mask_out);
+    bool host = gg->m > 0 && tc::is_host_pointer(mask_out);
     tc::Scratch sc(s);
     uint8_t* mask = mask_out;
-    if (host) TC_TRY(sc.alloc(&mask, gg->m));
+    if (host) {
+        if (void* v = tc::host_device_view(mask_out)) {  // pinned: written in place
+            mask = static_cast<uint8_t*>(v);
+            host = false;
+        } else {
+            TC_TRY(sc.alloc(&mask, gg->m));
+        }
+    }
     int64_t left = 0;
     TC_TRY(tc::peel_ktruss(gg, k, mask, &left, s));
     if (host) TC_TRY(deliver(mask_out, mask, gg->m, s));
@@ -318,7 +351,13 @@ int ktruss_max(tc_graph* g, int32_t* kmax_out, int32_t* truss_out, void* cuda_st
     cudaStream_t s = as_stream(cuda_stream);
     tc::Scratch sc(s);
     int32_t* truss = truss_out;
-    const bool direct = truss_out && gg->m > 0 && !tc::is_host_pointer(truss_out);
+    bool direct = truss_out && gg->m > 0 && !tc::is_host_pointer(truss_out);
+    if (!direct && truss_out && gg->m > 0) {
+        if (void* v = tc::host_device_view(truss_out)) {  // pinned: written in place
+            truss = static_cast<int32_t*>(v);
+            direct = true;
+        }
+    }
     if (!direct) TC_TRY(sc.alloc(&truss, gg->m));
     int32_t kmax = 0;
     TC_TRY(tc::peel_decompose(gg, truss, &kmax, s));

@@ -100,6 +100,7 @@ struct Scratch {
 // Pointer location: true if `p` is host memory the device cannot address
 // directly as device memory (pageable, or pinned/registered host memory).
 bool is_host_pointer(const void* p);
+void* host_device_view(const void* p);  // device address of pinned host memory, else nullptr
 
 // ---------------------------------------------------------------- device helpers
 
