@@ -17,9 +17,10 @@
  *    edge id, and every per-edge output is indexed by it.
  *  - Pointers: the caller owns every input and output buffer.  Array
  *    arguments may be device memory or host memory (pageable or pinned);
- *    the library inspects each pointer and copies through the device when
- *    it is on the host.  Scalar outputs (triangles_out, edges_out,
- *    kmax_out) are host pointers.
+ *    the library inspects each pointer.  Pinned or registered host memory
+ *    (mapped into the device's address space) is read or written in place
+ *    by the kernels; pageable host memory is copied through the device.
+ *    Scalar outputs (triangles_out, edges_out, kmax_out) are host pointers.
  *  - Streams: `cuda_stream` is a cudaStream_t (NULL = the legacy default
  *    stream).  Work is ordered on that stream.  A call that returns a host
  *    scalar, or writes a host array, synchronises that stream before
